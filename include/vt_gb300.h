@@ -1,0 +1,171 @@
+/*
+ * vt_gb300.h -- C ABI of the GB300 (sm_103a) Voronoi-cell library.
+ *
+ * What the library computes follows PARAVT (R. E. Gonzalez, "PARAVT: Parallel
+ * Voronoi Tessellation code", arXiv:1601.06429):
+ *   - the Voronoi cell of every particle, i.e. the region nearer to it than
+ *     to any other particle (Introduction), in a periodic box (Abstract and
+ *     Discussion: periodic conditions) or a bounded box;
+ *   - from each cell its volume and the density mass/volume (Implementation
+ *     section: volume from the cell facets, density from particle mass and
+ *     cell volume), the immediate neighbours, i.e. the particles that share a
+ *     facet (Implementation section), the density gradient from densities and
+ *     neighbours (Implementation section) and densities on a regular grid
+ *     (Implementation section);
+ *   - outputs are in input order and neighbour indices are real particle
+ *     indices, never periodic images (Implementation section: re-indexing of
+ *     boundary particles to real indices, output in input order).
+ * The backward pass (vt_backward) has no counterpart in the paper; it is the
+ * derivative of the cell volumes with respect to the particle positions.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" are CUDA device memory on the current device,
+ *     owned by the caller, and must stay valid until the call's work on the
+ *     handle's stream has finished.  Pointers marked "host" are read or written
+ *     before the call returns.
+ *   - Positions are [N][3] row-major (x,y,z per particle), FP32 or FP64 as
+ *     given by `dtype`; every floating-point output uses the same dtype.
+ *   - Return value: VT_OK (0) or a negative VT_ERR_* code.  No exception and
+ *     no device trap crosses this boundary; errors detected on the device are
+ *     recorded in the handle and returned by the next call that synchronises
+ *     (vt_build, the size query of vt_cells, vt_status).
+ *   - Work is enqueued on the stream given to vt_build.  vt_build returns after
+ *     one synchronisation (it reads a few status words back); the other calls
+ *     are asynchronous unless stated.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef VT_GB300_H
+#define VT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define VT_OK 0
+#define VT_ERR_INVALID -1     /* bad argument, NaN/out-of-box position, bad handle */
+#define VT_ERR_OOM -2         /* device allocation failed */
+#define VT_ERR_CUDA -3        /* a CUDA runtime call failed */
+#define VT_ERR_DUPLICATE -4   /* two particles at the same position */
+#define VT_ERR_SECURITY -5    /* the security-radius test did not pass within max_passes */
+#define VT_ERR_UNSUPPORTED -6 /* e.g. a periodic cell wider than a quarter box, FP32 filter with a box length not representable in FP32 */
+#define VT_ERR_CAPACITY -7    /* a cell exceeded the per-cell plane, vertex or candidate capacity */
+#define VT_ERR_NUMERIC -8     /* an exact-arithmetic expansion exceeded its workspace */
+
+/* position / output dtypes */
+#define VT_F32 0
+#define VT_F64 1
+
+/* clipping precision */
+#define VT_PLAIN64 0  /* FP64 geometry; FP64 error-bounded predicates, exact fallback */
+#define VT_FILTER32 1 /* FP32 geometry; FP32 error-bounded predicates, FP64 then exact fallback */
+
+typedef struct vt_params {
+    int precision;  /* VT_PLAIN64 or VT_FILTER32 (default VT_FILTER32) */
+    int k_target;   /* particles aimed for in a cell's first candidate pass (default 40) */
+    int max_passes; /* candidate radius passes per cell before VT_ERR_SECURITY (default 24) */
+    int face_pool;  /* facet records reserved per particle (default 24; grown on demand) */
+    int reserved[4];
+} vt_params;
+
+typedef struct vt_stats {
+    int64_t n;                /* particles */
+    int64_t n_faces;          /* facets between particles (each counted from both sides) */
+    int64_t n_cut;            /* bisector planes that cut a cell */
+    int64_t n_tested;         /* bisector planes tested against a cell */
+    int64_t n_passes;         /* candidate radius passes, summed over cells */
+    int64_t n_fp64_fallbacks; /* FP32 predicates re-decided in FP64 */
+    int64_t n_exact_cells;    /* cells re-run with the exact predicate */
+    int64_t n_exact_preds;    /* predicates decided by exact expansion arithmetic */
+    int64_t n_exact_zero;     /* exact predicates that were zero (degenerate input) */
+    int64_t max_faces;        /* largest facet count of a cell */
+    int32_t device_error;     /* first VT_ERR_* recorded on the device, or VT_OK */
+    int32_t error_particle;   /* an input index that raised it, or -1 */
+    int64_t reserved[6];
+} vt_stats;
+
+typedef struct vt_handle_s *vt_handle;
+
+/* Fill *p with the defaults.  Returns VT_OK or VT_ERR_INVALID (p == NULL). */
+int vt_default_params(vt_params *p);
+
+/*
+ * vt_build -- Voronoi cells of all N particles (Implementation section: the
+ * tessellation step; here per cell, by clipping with bisector planes).
+ *   h       host out: new handle (NULL on failure)
+ *   pos     device [N][3], dtype VT_F32 or VT_F64.  Periodic: every coordinate
+ *           in [box_lo, box_hi); bounded: in [box_lo, box_hi].
+ *   mass    device [N] of the same dtype, or NULL for unit masses
+ *   box_lo, box_hi  host [3]: box corners (box_hi > box_lo)
+ *   periodic 1: periodic box; 0: cells clipped by the box walls
+ *   p       host params or NULL for defaults
+ *   stream  cudaStream_t (NULL: legacy default stream)
+ * The handle owns its workspace (sorted particles, search tree, facet records)
+ * until vt_destroy.  `pos` and `mass` are read during the call only.  Errors:
+ * VT_ERR_INVALID (arguments, NaN or out-of-box coordinates), VT_ERR_DUPLICATE,
+ * VT_ERR_SECURITY, VT_ERR_UNSUPPORTED, VT_ERR_CAPACITY, VT_ERR_NUMERIC,
+ * VT_ERR_OOM, VT_ERR_CUDA; on error *h is NULL and nothing is leaked.
+ */
+int vt_build(vt_handle *h, const void *pos, int dtype, const void *mass, int64_t N, const double box_lo[3],
+             const double box_hi[3], int periodic, const vt_params *p, void *stream);
+
+/*
+ * vt_cells -- cell volumes and neighbour lists (Implementation section:
+ * volume from the facets; neighbours are the particles sharing a facet;
+ * output in input order with real indices).
+ *   vol          device [N] (dtype of pos) or NULL
+ *   nbr_off      device int64 [N+1] CSR offsets or NULL
+ *   nbr_id       device int32 [nnz]: neighbours of particle i, ascending, at
+ *                nbr_id[nbr_off[i] .. nbr_off[i+1]); NULL = size query
+ *   n_faces_out  host out: nnz (always written when non-NULL; the size query
+ *                needs no synchronisation: the count is known after vt_build)
+ */
+int vt_cells(vt_handle h, void *vol, int64_t *nbr_off, int32_t *nbr_id, int64_t *n_faces_out);
+
+/* vt_density -- density mass/volume (Implementation section).  dens: device [N]. */
+int vt_density(vt_handle h, void *dens);
+
+/*
+ * vt_gradient -- density gradient at each particle from the densities of its
+ * Voronoi neighbours (Implementation section; the paper gives no formula):
+ * the least-squares linear fit  (sum_j d d^T) g = sum_j d (rho_j - rho_i),
+ * d = x_j - x_i the facet's image displacement.  grad: device [N][3].
+ */
+int vt_gradient(vt_handle h, void *grad);
+
+/*
+ * vt_grid_density -- densities on a regular G^3 grid over the box
+ * (Implementation section; the paper gives no formula): node (a,b,c) takes
+ * the mean, over its S^3 stratified sub-points
+ * lo + (a + (u+1/2)/S) L/G ..., of the density of the cell containing the
+ * sub-point (the nearest particle; ties to the lower index).
+ * grid: device [G][G][G] indexed [c][b][a] (x fastest).  1 <= G <= 4096, 1 <= S <= 8.
+ */
+int vt_grid_density(vt_handle h, int G, int S, void *grid);
+
+/*
+ * vt_backward -- adjoint of the cell volumes (no counterpart in the paper).
+ * For a loss L with dL/dV_i = dL_dV[i] and, optionally, a uniform weight
+ * dL_dE on the centroidal (CVT) energy E = sum_i integral_{cell i} |y - x_i|^2:
+ *   dL/dx_k = sum_{j in N(k)} (A_kj/|r_kj|) (g_k - g_j) (c_kj - x_k)
+ *             + dL_dE * 2 V_k (x_k - z_k),
+ * with A, c the facet area and centroid, r the separation and z the cell
+ * centroid.  dL_dV: device [N] or NULL; dL_dpos: device [N][3] (overwritten).
+ */
+int vt_backward(vt_handle h, const void *dL_dV, double dL_dE, void *dL_dpos);
+
+/* vt_status -- counters and the sticky device error; synchronises the stream. */
+int vt_status(vt_handle h, vt_stats *out);
+
+/* vt_error_string -- static description of a VT_* code. */
+const char *vt_error_string(int code);
+
+/* vt_destroy -- frees the handle and its workspace (NULL is ignored). */
+void vt_destroy(vt_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VT_GB300_H */

@@ -671,7 +671,10 @@ static int run_certified(cellwork *cw, const kdtree *t, candbuf *cb, int64_t lea
     double r_lo2 = 0.0;
     int smax = pb->periodic ? 1 : 0;
     for (int pass = 0; pass < 64; pass++) {
-        if (pb->periodic && r > 1.5 * lmin) return run_brute(cw, cb);
+        if (pb->periodic && r > 1.5 * lmin) {
+            init_cell(cw); /* start over with every image */
+            return run_brute(cw, cb);
+        }
         double r_hi2 = r * r;
         cb->n = 0;
         for (int sx = -smax; sx <= smax; sx++)
@@ -687,9 +690,11 @@ static int run_certified(cellwork *cw, const kdtree *t, candbuf *cb, int64_t lea
          * |d| >= r (1 - 2 eps) - margin.  Done when that is >= 2 R. */
         double R = sqrt(rmax2_upper(cw)) * (1.0 + 4 * eps);
         if (r * (1.0 - 4 * eps) - 2.0 * margin >= 2.0 * R) return 0;
+        /* next pass: the annulus up to 2R, but at most twice the radius (a cell that is
+         * still open after a few candidates closes with a few more) */
         r_lo2 = r_hi2;
         double rn = 2.0 * R * (1.0 + 1e-12) + 4.0 * margin;
-        r = rn > 1.25 * r ? rn : 1.25 * r;
+        r = rn < 2.0 * r ? rn : 2.0 * r;
     }
     return OE_NUM;
 }

@@ -1,0 +1,260 @@
+"""Thin Python binding of the C ABI in ``include/vt_gb300.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; all the
+work happens in the CUDA kernels behind them.  Tensors are torch CUDA tensors
+(PyTorch supplies device memory and the stream).  If the compiled library is
+missing the functions raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvt_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "vt_gb300.h")
+
+VT_OK = 0
+VT_ERR_INVALID = -1
+VT_ERR_OOM = -2
+VT_ERR_CUDA = -3
+VT_ERR_DUPLICATE = -4
+VT_ERR_SECURITY = -5
+VT_ERR_UNSUPPORTED = -6
+VT_ERR_CAPACITY = -7
+VT_ERR_NUMERIC = -8
+VT_F32 = 0
+VT_F64 = 1
+VT_PLAIN64 = 0
+VT_FILTER32 = 1
+
+
+class vt_params(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("k_target", ctypes.c_int), ("max_passes", ctypes.c_int),
+                ("face_pool", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class vt_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("n_cut", ctypes.c_int64),
+                ("n_tested", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_fp64_fallbacks", ctypes.c_int64),
+                ("n_exact_cells", ctypes.c_int64), ("n_exact_preds", ctypes.c_int64),
+                ("n_exact_zero", ctypes.c_int64), ("max_faces", ctypes.c_int64), ("device_error", ctypes.c_int32),
+                ("error_particle", ctypes.c_int32), ("reserved", ctypes.c_int64 * 6)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class VTError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = int(code)
+        msg = error_string(code)
+        super().__init__("%s: %s (%d)" % (where or "vt", msg, code))
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``libvt_gb300.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libvt_gb300.so not found at %s: build it with paper_1601_06429_gb300.build.build()"
+                           % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32 = ctypes.c_int
+    i64 = ctypes.c_int64
+    lib.vt_default_params.argtypes = [ctypes.POINTER(vt_params)]
+    lib.vt_default_params.restype = i32
+    lib.vt_build.argtypes = [ctypes.POINTER(P), P, i32, P, i64, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(vt_params), P]
+    lib.vt_build.restype = i32
+    lib.vt_cells.argtypes = [P, P, P, P, ctypes.POINTER(i64)]
+    lib.vt_cells.restype = i32
+    lib.vt_density.argtypes = [P, P]
+    lib.vt_density.restype = i32
+    lib.vt_gradient.argtypes = [P, P]
+    lib.vt_gradient.restype = i32
+    lib.vt_grid_density.argtypes = [P, i32, i32, P]
+    lib.vt_grid_density.restype = i32
+    lib.vt_backward.argtypes = [P, P, ctypes.c_double, P]
+    lib.vt_backward.restype = i32
+    lib.vt_status.argtypes = [P, ctypes.POINTER(vt_stats)]
+    lib.vt_status.restype = i32
+    lib.vt_error_string.argtypes = [i32]
+    lib.vt_error_string.restype = ctypes.c_char_p
+    lib.vt_destroy.argtypes = [P]
+    lib.vt_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def header_symbols(path: str = HEADER):
+    """Names of the entry points declared in the public header."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(vt_[a-z_]+)\s*\(", txt)))
+
+
+def error_string(code: int) -> str:
+    try:
+        return load_library().vt_error_string(int(code)).decode()
+    except Exception:  # library missing: still describe the code
+        return "code %d" % code
+
+
+def _check(rc, where):
+    if rc != VT_OK:
+        raise VTError(rc, where)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def vt_default_params() -> vt_params:
+    p = vt_params()
+    _check(load_library().vt_default_params(ctypes.byref(p)), "vt_default_params")
+    return p
+
+
+class Handle:
+    """Owns a ``vt_handle``; destroyed with the object (or by :func:`vt_destroy`)."""
+
+    def __init__(self, ptr, N, dtype, device, stream):
+        self.ptr = ptr
+        self.N = N
+        self.dtype = dtype
+        self.device = device
+        self.stream = stream
+
+    def __del__(self):
+        try:
+            vt_destroy(self)
+        except Exception:
+            pass
+
+
+def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), periodic=True, precision="filter32",
+             k_target=40, max_passes=24, face_pool=24, stream=None) -> Handle:
+    """Voronoi cells of all particles; ``pos`` is a CUDA [N,3] float32/float64 tensor."""
+    import torch
+
+    lib = load_library()
+    if not (isinstance(pos, torch.Tensor) and pos.is_cuda and pos.dim() == 2 and pos.shape[1] == 3):
+        raise VTError(VT_ERR_INVALID, "vt_build: pos must be a CUDA [N,3] tensor")
+    if pos.dtype not in (torch.float32, torch.float64):
+        raise VTError(VT_ERR_INVALID, "vt_build: pos dtype")
+    pos = pos.contiguous()
+    if mass is not None:
+        mass = mass.to(device=pos.device, dtype=pos.dtype).contiguous()
+    p = vt_default_params()
+    p.precision = {"filter32": VT_FILTER32, "plain64": VT_PLAIN64}[precision] if isinstance(precision, str) \
+        else int(precision)
+    p.k_target = int(k_target)
+    p.max_passes = int(max_passes)
+    p.face_pool = int(face_pool)
+    lo = (ctypes.c_double * 3)(*[float(v) for v in (box_lo if hasattr(box_lo, "__len__") else (box_lo,) * 3)])
+    hi = (ctypes.c_double * 3)(*[float(v) for v in (box_hi if hasattr(box_hi, "__len__") else (box_hi,) * 3)])
+    h = ctypes.c_void_p()
+    dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
+    with torch.cuda.device(pos.device):
+        rc = lib.vt_build(ctypes.byref(h), _ptr(pos), dt, _ptr(mass), pos.shape[0], lo, hi, int(bool(periodic)),
+                          ctypes.byref(p), _stream_ptr(stream))
+    _check(rc, "vt_build")
+    return Handle(h, pos.shape[0], pos.dtype, pos.device, stream)
+
+
+def vt_cells(h: Handle, vol=None, nbr_off=None, nbr_id=None) -> int:
+    """Fill any of ``vol`` [N], ``nbr_off`` int64 [N+1], ``nbr_id`` int32 [nnz]; returns nnz."""
+    n = ctypes.c_int64(0)
+    _check(load_library().vt_cells(h.ptr, _ptr(vol), _ptr(nbr_off), _ptr(nbr_id), ctypes.byref(n)), "vt_cells")
+    return int(n.value)
+
+
+def vt_density(h: Handle, dens) -> None:
+    _check(load_library().vt_density(h.ptr, _ptr(dens)), "vt_density")
+
+
+def vt_gradient(h: Handle, grad) -> None:
+    _check(load_library().vt_gradient(h.ptr, _ptr(grad)), "vt_gradient")
+
+
+def vt_grid_density(h: Handle, G: int, S: int, grid) -> None:
+    _check(load_library().vt_grid_density(h.ptr, int(G), int(S), _ptr(grid)), "vt_grid_density")
+
+
+def vt_backward(h: Handle, dL_dV, dL_dE: float, dL_dpos) -> None:
+    _check(load_library().vt_backward(h.ptr, _ptr(dL_dV), float(dL_dE), _ptr(dL_dpos)), "vt_backward")
+
+
+def vt_status(h: Handle) -> dict:
+    st = vt_stats()
+    rc = load_library().vt_status(h.ptr, ctypes.byref(st))
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def vt_destroy(h: Handle) -> None:
+    if h is not None and h.ptr is not None and h.ptr.value:
+        load_library().vt_destroy(h.ptr)
+        h.ptr = None
+
+
+# ---------------------------------------------------------------- convenience wrappers
+def cells(h: Handle):
+    """(vol [N], nbr_off int64 [N+1], nbr_id int32 [nnz]) as new CUDA tensors."""
+    import torch
+
+    nnz = vt_cells(h)
+    vol = torch.empty(h.N, dtype=h.dtype, device=h.device)
+    off = torch.empty(h.N + 1, dtype=torch.int64, device=h.device)
+    ids = torch.empty(max(nnz, 1), dtype=torch.int32, device=h.device)
+    vt_cells(h, vol, off, ids)
+    return vol, off, ids[:nnz]
+
+
+def density(h: Handle):
+    import torch
+
+    d = torch.empty(h.N, dtype=h.dtype, device=h.device)
+    vt_density(h, d)
+    return d
+
+
+def gradient(h: Handle):
+    import torch
+
+    g = torch.empty(h.N, 3, dtype=h.dtype, device=h.device)
+    vt_gradient(h, g)
+    return g
+
+
+def grid_density(h: Handle, G: int, S: int = 1):
+    import torch
+
+    g = torch.empty(G, G, G, dtype=h.dtype, device=h.device)
+    vt_grid_density(h, G, S, g)
+    return g
+
+
+def backward(h: Handle, dL_dV=None, dL_dE: float = 0.0):
+    import torch
+
+    out = torch.empty(h.N, 3, dtype=h.dtype, device=h.device)
+    if dL_dV is not None:
+        dL_dV = dL_dV.to(device=h.device, dtype=h.dtype).contiguous()
+    vt_backward(h, dL_dV, dL_dE, out)
+    return out

@@ -1,0 +1,332 @@
+// vt_api.cu -- the C ABI (see include/vt_gb300.h): handle, workspace, launch order, error reporting.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "vt_internal.cuh"
+#include "vt_kernels.cuh"
+
+using namespace vt;
+
+namespace {
+
+constexpr int RC_POOL_HOST = 1001;  // device code for "facet pool too small" (the host grows it)
+
+struct Alloc {
+    bool failed = false;
+    template <typename T>
+    T* get(size_t count) {
+        if (count == 0) count = 1;
+        void* p = nullptr;
+        if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            failed = true;
+            return nullptr;
+        }
+        return (T*)p;
+    }
+};
+
+void free_handle(vt_handle h) {
+    if (!h) return;
+    void* ptrs[] = {h->spos, h->perm, h->inv, h->tree_mem, h->cell, h->face_start, h->face_count, h->cstat,
+                    h->exact_list, h->dens_sorted, h->faces, h->xws, h->tmp, h->nbr_off_cache, h->dstat,
+                    h->keys, h->keys_alt, h->vals_alt, h->cnt_in};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return VT_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? VT_ERR_OOM : VT_ERR_CUDA;
+}
+
+ClipArgs clip_args(vt_handle h) {
+    ClipArgs a;
+    a.spos = h->spos;
+    a.N = h->N;
+    a.geo = h->geo;
+    a.tree = h->tree;
+    a.k_target = h->prm.k_target;
+    a.max_passes = h->prm.max_passes;
+    a.cell = h->cell;
+    a.face_start = h->face_start;
+    a.face_count = h->face_count;
+    a.cstat = h->cstat;
+    a.exact_list = h->exact_list;
+    a.faces = h->faces;
+    a.face_cap = h->face_cap;
+    a.st = h->dstat;
+    a.xws = h->xws;
+    a.xws_warps = h->xws_warps;
+    return a;
+}
+
+int run_clip(vt_handle h) {
+    cudaStream_t s = h->stream;
+    for (int attempt = 0; attempt < 4; attempt++) {
+        // reset the clipping counters (the input-validation count is kept)
+        DevStatus z;
+        memset(&z, 0, sizeof(z));
+        z.invalid_input = h->hstat.invalid_input;
+        z.error = h->hstat.error;
+        int rc = cuda_rc(cudaMemcpyAsync(h->dstat, &z, sizeof(z), cudaMemcpyHostToDevice, s));
+        if (rc) return rc;
+        rc = cuda_rc(cudaStreamSynchronize(s));
+        if (rc) return rc;
+        ClipArgs a = clip_args(h);
+        launch_clip(a, h->dtype, h->precision, h->sm_count, s);
+        launch_clip_exact(a, h->dtype, h->sm_count, s);
+        rc = cuda_rc(cudaGetLastError());
+        if (rc) return rc;
+        rc = cuda_rc(cudaMemcpyAsync(&h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        if (rc) return rc;
+        rc = cuda_rc(cudaStreamSynchronize(s));
+        if (rc) return rc;
+        if (h->hstat.error != RC_POOL_HOST) return h->hstat.error;
+        // facet pool too small: grow it and redo the cells
+        uint64_t need = h->hstat.face_next + (uint64_t)h->N * 4;
+        uint64_t cap = h->face_cap * 2 > need ? h->face_cap * 2 : need;
+        if (cap > 0xF0000000ull) return VT_ERR_CAPACITY;
+        cudaFree(h->faces);
+        h->faces = nullptr;
+        if (cudaMalloc((void**)&h->faces, cap * sizeof(Face)) != cudaSuccess) {
+            cudaGetLastError();
+            return VT_ERR_OOM;
+        }
+        h->face_cap = cap;
+        h->hstat.error = 0;
+    }
+    return VT_ERR_CAPACITY;
+}
+
+__global__ void k_set_i64(int64_t* p, int64_t v) { *p = v; }
+
+int ensure_density(vt_handle h) {
+    if (h->dens_ready) return VT_OK;
+    launch_density(h->cell, h->spos, h->dtype, h->perm, h->N, h->dens_sorted, nullptr, h->stream);
+    h->dens_ready = 1;
+    return cuda_rc(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+int vt_default_params(vt_params* p) {
+    if (!p) return VT_ERR_INVALID;
+    memset(p, 0, sizeof(*p));
+    p->precision = VT_FILTER32;
+    p->k_target = 40;
+    p->max_passes = 24;
+    p->face_pool = 24;
+    return VT_OK;
+}
+
+int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64_t N, const double box_lo[3],
+             const double box_hi[3], int periodic, const vt_params* p, void* stream) {
+    if (!out) return VT_ERR_INVALID;
+    *out = nullptr;
+    if (!pos || !box_lo || !box_hi || N < 1 || N > 0x7FFFFFFF / 2) return VT_ERR_INVALID;
+    if (dtype != VT_F32 && dtype != VT_F64) return VT_ERR_INVALID;
+    vt_params prm;
+    vt_default_params(&prm);
+    if (p) prm = *p;
+    if (prm.precision != VT_PLAIN64 && prm.precision != VT_FILTER32) return VT_ERR_INVALID;
+    if (prm.k_target < 8 || prm.k_target > 120 || prm.max_passes < 1 || prm.max_passes > 1000 || prm.face_pool < 1 ||
+        prm.face_pool > 128)
+        return VT_ERR_INVALID;
+    Geometry geo;
+    memset(&geo, 0, sizeof(geo));
+    for (int c = 0; c < 3; c++) {
+        if (!(box_hi[c] > box_lo[c]) || !isfinite(box_lo[c]) || !isfinite(box_hi[c])) return VT_ERR_INVALID;
+        geo.lo[c] = box_lo[c];
+        geo.hi[c] = box_hi[c];
+        geo.L[c] = box_hi[c] - box_lo[c];
+        geo.Lf[c] = (float)geo.L[c];
+        geo.halfLf[c] = 0.5f * geo.Lf[c];
+        geo.lof[c] = (float)box_lo[c];
+        geo.hif[c] = (float)box_hi[c];
+        if (prm.precision == VT_FILTER32 && periodic && (double)geo.Lf[c] != geo.L[c]) return VT_ERR_UNSUPPORTED;
+    }
+    geo.periodic = periodic ? 1 : 0;
+
+    vt_handle h = new (std::nothrow) vt_handle_s;
+    if (!h) return VT_ERR_OOM;
+    memset(h, 0, sizeof(*h));
+    h->N = N;
+    h->dtype = dtype;
+    h->precision = prm.precision;
+    h->prm = prm;
+    h->geo = geo;
+    h->stream = (cudaStream_t)stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (h->sm_count <= 0) h->sm_count = 1;
+
+    Alloc A;
+    size_t psz = dtype == VT_F32 ? sizeof(float4) : sizeof(dpt4);
+    h->spos = A.get<unsigned char>(N * psz);
+    h->keys = A.get<uint64_t>(N);
+    h->keys_alt = A.get<uint64_t>(N);
+    h->perm = A.get<uint32_t>(N);
+    h->vals_alt = A.get<uint32_t>(N);
+    h->inv = A.get<uint32_t>(N);
+    tree_layout(N, h->tree);
+    h->tree_mem = A.get<float4>(2 * h->tree.off[0]);
+    h->tree.lo = h->tree_mem;
+    h->tree.hi = h->tree_mem ? h->tree_mem + h->tree.off[0] : nullptr;
+    h->cell = A.get<CellOut>(N);
+    h->face_start = A.get<uint32_t>(N);
+    h->face_count = A.get<uint16_t>(N);
+    h->cnt_in = A.get<uint16_t>(N);
+    h->cstat = A.get<uint8_t>(N);
+    h->exact_list = A.get<uint32_t>(N);
+    h->dens_sorted = A.get<double>(N);
+    h->face_cap = (uint64_t)N * prm.face_pool;
+    h->faces = A.get<Face>(h->face_cap);
+    h->xws_warps = h->sm_count * 4;
+    h->xws = A.get<double>((size_t)h->xws_warps * exact_ws_doubles_per_warp());
+    size_t tb = radix_tmp_bytes(N);
+    size_t sb = scan_tmp_bytes(N + 1);
+    h->tmp_bytes = tb > sb ? tb : sb;
+    h->tmp = A.get<unsigned char>(h->tmp_bytes);
+    h->dstat = A.get<DevStatus>(1);
+    if (A.failed) {
+        free_handle(h);
+        return VT_ERR_OOM;
+    }
+    cudaStream_t s = h->stream;
+    memset(&h->hstat, 0, sizeof(h->hstat));
+    int rc = cuda_rc(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), s));
+    if (!rc) {
+        launch_key(pos, dtype, N, geo, h->keys, h->perm, h->dstat, s);
+        radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48, h->tmp, s);
+        launch_gather(pos, mass, dtype, h->perm, N, h->spos, h->inv, s);
+        launch_tree(h->spos, dtype, N, h->tree, s);
+        rc = cuda_rc(cudaGetLastError());
+    }
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(&h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(s));
+    if (!rc && h->hstat.invalid_input) rc = VT_ERR_INVALID;
+    if (!rc) rc = run_clip(h);
+    if (rc) {
+        free_handle(h);
+        return rc;
+    }
+    h->n_faces = (int64_t)h->hstat.n_faces;
+    *out = h;
+    return VT_OK;
+}
+
+int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t* n_faces_out) {
+    if (!h) return VT_ERR_INVALID;
+    cudaStream_t s = h->stream;
+    if (n_faces_out) *n_faces_out = h->n_faces;
+    if (vol) launch_out_vol(h->cell, h->perm, h->N, vol, h->dtype, s);
+    if (nbr_off || nbr_id) {
+        int64_t* off = nbr_off;
+        if (!off) {
+            if (!h->nbr_off_cache && cudaMalloc((void**)&h->nbr_off_cache, (h->N + 1) * sizeof(int64_t)) != cudaSuccess) {
+                cudaGetLastError();
+                h->nbr_off_cache = nullptr;
+                return VT_ERR_OOM;
+            }
+            off = h->nbr_off_cache;
+        }
+        launch_nbr_count(h->face_count, h->inv, h->N, h->cnt_in, s);
+        scan_u16_i64(h->cnt_in, off, h->N, h->tmp, s);
+        k_set_i64<<<1, 1, 0, s>>>(off + h->N, h->n_faces);
+        if (nbr_id) launch_nbr_emit(h->faces, h->face_start, h->face_count, h->perm, h->inv, off, h->N, nbr_id, s);
+    }
+    return cuda_rc(cudaGetLastError());
+}
+
+int vt_density(vt_handle h, void* dens) {
+    if (!h || !dens) return VT_ERR_INVALID;
+    launch_density(h->cell, h->spos, h->dtype, h->perm, h->N, h->dens_sorted, dens, h->stream);
+    h->dens_ready = 1;
+    return cuda_rc(cudaGetLastError());
+}
+
+int vt_gradient(vt_handle h, void* grad) {
+    if (!h || !grad) return VT_ERR_INVALID;
+    int rc = ensure_density(h);
+    if (rc) return rc;
+    launch_gradient(h->faces, h->face_start, h->face_count, h->dens_sorted, h->perm, h->N, grad, h->dtype, h->stream);
+    return cuda_rc(cudaGetLastError());
+}
+
+int vt_grid_density(vt_handle h, int G, int S, void* grid) {
+    if (!h || !grid || G < 1 || G > 4096 || S < 1 || S > 8) return VT_ERR_INVALID;
+    if ((int64_t)G * G * G > ((int64_t)1 << 34)) return VT_ERR_INVALID;
+    int rc = ensure_density(h);
+    if (rc) return rc;
+    launch_grid(h->spos, h->dtype, h->N, h->geo, h->tree, h->dens_sorted, h->perm, G, S, grid, h->dstat, h->sm_count,
+                h->stream);
+    return cuda_rc(cudaGetLastError());
+}
+
+int vt_backward(vt_handle h, const void* dL_dV, double dL_dE, void* dL_dpos) {
+    if (!h || !dL_dpos || !isfinite(dL_dE)) return VT_ERR_INVALID;
+    launch_backward(h->faces, h->face_start, h->face_count, h->cell, h->spos, h->dtype, h->perm, h->inv, h->N, dL_dV,
+                    dL_dE, dL_dpos, h->stream);
+    return cuda_rc(cudaGetLastError());
+}
+
+int vt_status(vt_handle h, vt_stats* out) {
+    if (!h || !out) return VT_ERR_INVALID;
+    DevStatus d;
+    int rc = cuda_rc(cudaMemcpyAsync(&d, h->dstat, sizeof(d), cudaMemcpyDeviceToHost, h->stream));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    if (rc) return rc;
+    memset(out, 0, sizeof(*out));
+    out->n = h->N;
+    out->n_faces = (int64_t)d.n_faces;
+    out->n_cut = (int64_t)d.n_cut;
+    out->n_tested = (int64_t)d.n_tested;
+    out->n_passes = (int64_t)d.n_passes;
+    out->n_fp64_fallbacks = (int64_t)d.n_fp64;
+    out->n_exact_cells = (int64_t)d.n_exact_cells;
+    out->n_exact_preds = (int64_t)d.n_exact_preds;
+    out->n_exact_zero = (int64_t)d.n_exact_zero;
+    out->max_faces = (int64_t)d.max_faces;
+    out->device_error = d.error;
+    out->error_particle = -1;
+    if (d.error && d.error_cell >= 0 && d.error_cell < h->N) {
+        uint32_t pi = 0;
+        if (cudaMemcpy(&pi, h->perm + d.error_cell, sizeof(pi), cudaMemcpyDeviceToHost) == cudaSuccess)
+            out->error_particle = (int32_t)pi;
+    }
+    return d.error ? d.error : VT_OK;
+}
+
+const char* vt_error_string(int code) {
+    switch (code) {
+        case VT_OK: return "ok";
+        case VT_ERR_INVALID: return "invalid argument or input (NaN, out-of-box coordinate, bad handle)";
+        case VT_ERR_OOM: return "device allocation failed";
+        case VT_ERR_CUDA: return "CUDA runtime error";
+        case VT_ERR_DUPLICATE: return "two particles at the same position";
+        case VT_ERR_SECURITY: return "security-radius test did not pass within max_passes";
+        case VT_ERR_UNSUPPORTED: return "unsupported configuration (periodic cell wider than a quarter box, or box length not representable in FP32 for the FP32 filter)";
+        case VT_ERR_CAPACITY: return "per-cell capacity exceeded (planes, vertices, candidates or facet pool)";
+        case VT_ERR_NUMERIC: return "exact-arithmetic workspace exceeded";
+        default: return "unknown error code";
+    }
+}
+
+void vt_destroy(vt_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_handle(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// vt_internal.cuh -- shared declarations of the GB300 Voronoi library (device side + handle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vt_gb300.h"
+
+namespace vt {
+
+constexpr int WARP = 32;
+constexpr int MAXT = 128;       // triangle (vertex) slots per cell: 4 per lane
+constexpr int TPL = MAXT / WARP;
+constexpr int MAXP = 128;       // planes that may cut one cell (ids are 8-bit)
+constexpr int CAND_CAP = 128;   // candidates per radius pass
+constexpr int STACK_CAP = 192;  // tree traversal stack per warp
+constexpr int HASH_SZ = 512;    // directed-edge hash for facet walking
+constexpr int BUCKET = 32;      // particles per leaf bucket of the search tree
+constexpr int MAX_LEVELS = 8;
+
+// cell status bits (per sorted cell)
+constexpr uint8_t CS_DONE = 1;
+constexpr uint8_t CS_NEED_EXACT = 2;
+constexpr uint8_t CS_ERROR = 4;
+
+// device-side counters (reset by vt_build, read back at its end)
+struct DevStatus {
+    unsigned long long n_faces;
+    unsigned long long n_cut;
+    unsigned long long n_tested;
+    unsigned long long n_passes;
+    unsigned long long n_fp64;
+    unsigned long long n_exact_preds;
+    unsigned long long n_exact_zero;
+    unsigned long long face_next;    // next free facet record
+    unsigned int n_exact_cells;      // length of the exact-recompute list
+    unsigned int max_faces;
+    int error;                       // first VT_ERR_* (atomicCAS from 0)
+    int error_cell;                  // sorted index of that cell
+    unsigned int work_next;          // dynamic cell scheduler
+    unsigned int work_next_exact;
+    unsigned int invalid_input;      // count of NaN / out-of-box coordinates
+    unsigned int pad;
+};
+
+// facet record (one per cell side of a facet between two particles)
+struct __align__(16) Face {
+    float dx, dy, dz;      // displacement x_j (image) - x_i
+    float area;
+    float cx, cy, cz;      // facet centroid relative to x_i
+    uint32_t nbr;          // sorted index of the neighbour
+};
+
+// per-cell results in sorted order
+struct CellOut {
+    double vol;
+    float zx, zy, zz;      // cell centroid relative to x_i
+    float mom2;            // integral |y - x_i|^2 over the cell
+};
+
+struct Geometry {
+    double lo[3], hi[3], L[3];
+    float Lf[3], halfLf[3], lof[3], hif[3];
+    int periodic;
+};
+
+// search tree over sorted particles: level 1 = buckets of 32 particles, level l = 32 nodes of level l-1
+struct Tree {
+    int levels;                 // number of node levels (>= 1)
+    int64_t count[MAX_LEVELS + 1];
+    int64_t off[MAX_LEVELS + 1];  // offset of level l in the node arrays
+    float4* lo;                 // [total nodes] (x,y,z,-)
+    float4* hi;
+};
+
+}  // namespace vt
+
+struct vt_handle_s {
+    int64_t N;
+    int dtype;  // VT_F32 / VT_F64
+    int precision;
+    vt_params prm;
+    vt::Geometry geo;
+    cudaStream_t stream;
+    // sorted particles
+    void* spos;         // float4 (f32) or double4-like 4 doubles (f64): x,y,z,m
+    uint32_t* perm;     // sorted -> input index
+    uint32_t* inv;      // input -> sorted index
+    // search tree
+    vt::Tree tree;
+    float4* tree_mem;
+    // per-cell
+    vt::CellOut* cell;      // [N] sorted order
+    uint32_t* face_start;   // [N] sorted order
+    uint16_t* face_count;   // [N] sorted order
+    uint8_t* cstat;         // [N] sorted order
+    uint32_t* exact_list;   // [N]
+    double* dens_sorted;    // [N] sorted order
+    int dens_ready;
+    uint64_t* keys;         // [N] Morton keys (sort)
+    uint64_t* keys_alt;
+    uint32_t* vals_alt;
+    uint16_t* cnt_in;       // [N] facet counts in input order
+    vt::Face* faces;        // [face_cap]
+    uint64_t face_cap;
+    // exact workspace (per warp of the exact kernel)
+    double* xws;
+    int xws_warps;
+    // scratch for sort / scans
+    void* tmp;
+    size_t tmp_bytes;
+    int64_t* nbr_off_cache;  // [N+1] input order offsets (device)
+    int nbr_ready;
+    vt::DevStatus* dstat;   // device
+    vt::DevStatus hstat;    // host copy after build
+    int64_t n_faces;
+    int sm_count;
+};

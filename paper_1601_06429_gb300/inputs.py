@@ -104,23 +104,25 @@ def _isotropic(g, n):
 
 def _halo_counts(g, n_total, n_halo, slope=-1.9, span=1e3, nmin=20):
     """Particle counts per halo, proportional to power-law masses, >= nmin, summing to n_total."""
+    if n_halo * nmin > n_total:
+        raise ValueError("%d halos of at least %d particles do not fit in %d" % (n_halo, nmin, n_total))
     a = slope + 1.0
     u = g.random(n_halo)
     M = (1.0 + u * (span ** a - 1.0)) ** (1.0 / a)
     cnt = np.maximum(nmin, np.floor(M / M.sum() * n_total)).astype(np.int64)
-    # fix the total: add the remainder to the largest halos / remove from them
-    diff = n_total - cnt.sum()
+    # fix the total: remove the excess from the largest halos (never below nmin), or add the remainder to them
     order = np.argsort(-M)
-    k = 0
+    diff = int(n_total - cnt.sum())
     while diff != 0:
-        h = order[k % n_halo]
         if diff > 0:
-            cnt[h] += 1
-            diff -= 1
-        elif cnt[h] > nmin:
-            cnt[h] -= 1
-            diff += 1
-        k += 1
+            k = min(diff, n_halo)
+            cnt[order[:k]] += 1
+            diff -= k
+        else:
+            room = np.nonzero(cnt[order] > nmin)[0]
+            k = min(-diff, len(room))
+            cnt[order[room[:k]]] -= 1
+            diff += k
     return cnt
 
 
@@ -153,21 +155,28 @@ def _filaments(g, n_total, L, n_fil=1000, lmin=5.0, lmax=20.0, width=0.5):
     return start[fid] + t[:, None] * dv + off
 
 
-def clustered(N, L=100.0, seed=1, n_halo=2000, f_halo=0.60, f_fil=0.25, dtype=np.float32):
-    """Halo + filament + uniform mixture in a periodic box of side L."""
+def clustered(N, L=100.0, seed=1, n_halo=None, f_halo=0.60, f_fil=0.25, dtype=np.float32):
+    """Halo + filament + uniform mixture in a periodic box of side L.  2000 halos and 1000
+    filaments at 2,097,152 points; fewer (in proportion) for smaller sets, at least one."""
     g = rng(seed)
+    scale = min(1.0, N / 2097152.0)
+    if n_halo is None:
+        n_halo = max(1, int(round(2000 * scale)))
+    n_fil = max(1, int(round(1000 * scale)))
     nbar = N / L ** 3
     nh = int(round(f_halo * N))
     nf = int(round(f_fil * N))
     nu = N - nh - nf
-    x = np.concatenate([_halos(g, nh, n_halo, L, nbar), _filaments(g, nf, L), g.random((nu, 3)) * L])
+    x = np.concatenate([_halos(g, nh, n_halo, L, nbar), _filaments(g, nf, L, n_fil=n_fil), g.random((nu, 3)) * L])
     x = _wrap(x, L, dtype)
     x = x[g.permutation(N)]
     return _redraw_duplicates(x, L, g, dtype)
 
 
-def halo_uniform_mix(N, L=1.0, seed=3, f_halo=0.30, n_halo=2000, dtype=np.float32):
+def halo_uniform_mix(N, L=1.0, seed=3, f_halo=0.30, n_halo=None, dtype=np.float32):
     g = rng(seed)
+    if n_halo is None:
+        n_halo = max(1, int(round(2000 * min(1.0, N / 1048576.0))))
     nbar = N / L ** 3
     nh = int(round(f_halo * N))
     x = np.concatenate([_halos(g, nh, n_halo, L, nbar), g.random((N - nh, 3)) * L])

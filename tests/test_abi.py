@@ -1,0 +1,70 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point that include/vt_gb300.h declares; argument checks
+that return before any device work behave as documented.  No GPU needed."""
+import ctypes
+
+import pytest
+
+from paper_1601_06429_gb300 import binding
+from paper_1601_06429_gb300.build import build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return binding.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = binding.header_symbols()
+    assert {"vt_build", "vt_cells", "vt_density", "vt_gradient", "vt_grid_density", "vt_backward", "vt_status",
+            "vt_destroy", "vt_error_string", "vt_default_params"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_default_params_and_error_strings(lib):
+    p = binding.vt_default_params()
+    assert p.precision == binding.VT_FILTER32 and p.k_target == 40 and p.max_passes == 24 and p.face_pool == 24
+    assert lib.vt_default_params(None) == binding.VT_ERR_INVALID
+    for code in range(0, -9, -1):
+        assert binding.error_string(code) != "unknown error code"
+    assert binding.error_string(-99) == "unknown error code"
+
+
+def test_build_rejects_bad_arguments_without_device_work(lib):
+    h = ctypes.c_void_p(123)
+    lo = (ctypes.c_double * 3)(0, 0, 0)
+    hi = (ctypes.c_double * 3)(1, 1, 1)
+    bad_hi = (ctypes.c_double * 3)(1, 0, 1)
+    fake = ctypes.c_void_p(16)
+    assert lib.vt_build(None, fake, 0, None, 10, lo, hi, 1, None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_build(ctypes.byref(h), None, 0, None, 10, lo, hi, 1, None, None) == binding.VT_ERR_INVALID
+    assert h.value is None  # *h is cleared on error
+    assert lib.vt_build(ctypes.byref(h), fake, 0, None, 0, lo, hi, 1, None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_build(ctypes.byref(h), fake, 7, None, 10, lo, hi, 1, None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_build(ctypes.byref(h), fake, 0, None, 10, lo, bad_hi, 1, None, None) == binding.VT_ERR_INVALID
+    p = binding.vt_default_params()
+    p.k_target = 2
+    assert lib.vt_build(ctypes.byref(h), fake, 0, None, 10, lo, hi, 1, ctypes.byref(p), None) == binding.VT_ERR_INVALID
+    # FP32 filter needs a box length representable in FP32
+    p = binding.vt_default_params()
+    odd = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
+    assert lib.vt_build(ctypes.byref(h), fake, 0, None, 10, lo, odd, 1, ctypes.byref(p), None) == \
+        binding.VT_ERR_UNSUPPORTED
+
+
+def test_calls_reject_null_handle(lib):
+    assert lib.vt_cells(None, None, None, None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_density(None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_gradient(None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_grid_density(None, 8, 1, None) == binding.VT_ERR_INVALID
+    assert lib.vt_backward(None, None, 0.0, None) == binding.VT_ERR_INVALID
+    assert lib.vt_status(None, None) == binding.VT_ERR_INVALID
+    lib.vt_destroy(None)  # ignored
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(RuntimeError):
+        binding.load_library(str(tmp_path / "missing.so"))

@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (per particle, max over the compared particles):
+  * neighbour lists: identical sets (both sides decide every facet with
+    error-bounded predicates and an exact fallback, so the comparison is exact);
+  * volume and density: |d|/|ref| <= 1e-6 on the FP64 path, <= 2e-5 on the
+    FP32-filtered path;
+  * gradient: ||dg|| / max(||g_ref||, 1e-3 rho_i / l_i) <= 1e-4 on the FP64 path
+    (l_i = V_i^(1/3)); on the FP32 path the GPU densities themselves carry
+    relative errors up to 2e-5, which the least-squares fit turns into an
+    absolute gradient error of order 2e-5 * rho_i / l_i * k, so the floor is
+    raised to 1e-1 rho_i / l_i there (see the design notes);
+  * grid: the nearest particle is decided in FP64 with the same evaluation
+    order on both sides, so grid values are compared exactly.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1601_06429_gb300 import binding as vt
+from paper_1601_06429_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1601_06429_gb300.build import build
+
+    build()
+    vt.load_library()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def gpu_run(x, lo, hi, periodic=True, precision="plain64", mass=None, grid=None, **kw):
+    pos = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    m = None if mass is None else torch.from_numpy(np.ascontiguousarray(mass)).cuda()
+    h = vt.vt_build(pos, m, (lo,) * 3, (hi,) * 3, periodic, precision, **kw)
+    vol, off, ids = vt.cells(h)
+    dens = vt.density(h)
+    grad = vt.gradient(h)
+    out = dict(h=h, vol=vol.cpu().numpy().astype(np.float64), off=off.cpu().numpy(), ids=ids.cpu().numpy(),
+               dens=dens.cpu().numpy().astype(np.float64), grad=grad.cpu().numpy().astype(np.float64))
+    if grid is not None:
+        out["grid"] = vt.grid_density(h, grid[0], grid[1]).cpu().numpy().astype(np.float64)
+    out["stats"] = vt.vt_status(h)
+    return out
+
+
+def check_cells(g, o, oracle_mod, which, vol_tol):
+    ooff, oids = oracle_mod.neighbours(o)
+    vr = np.abs(g["vol"][which] - o["vol"]) / o["vol"]
+    assert vr.max() <= vol_tol, "volume rel err %g" % vr.max()
+    bad = 0
+    for k, i in enumerate(which):
+        a = g["ids"][g["off"][i]:g["off"][i + 1]]
+        b = oids[ooff[k]:ooff[k + 1]]
+        if not np.array_equal(a, b):
+            bad += 1
+    assert bad == 0, "%d cells with neighbour lists different from the oracle" % bad
+
+
+def check_gradient(g, x, o, oracle_mod, which, lo, hi, floor, tol):
+    dens_o = oracle_mod.density(np.ones(len(which)), o["vol"])
+    noff, nids, disp = oracle_mod.neighbour_displacements(o, x.astype(np.float64), lo, hi)
+    # the oracle gradient needs rho_j of every neighbour: take the GPU-independent oracle volumes
+    assert len(which) == len(x)
+    g_ref = oracle_mod.gradient(dens_o, noff, nids, disp, dens_o)
+    ell = o["vol"] ** (1.0 / 3.0)
+    den = np.maximum(np.linalg.norm(g_ref, axis=1), floor * dens_o / ell)
+    err = np.linalg.norm(g["grad"] - g_ref, axis=1) / den
+    assert err.max() <= tol, "gradient err %g" % err.max()
+
+
+# ---------------------------------------------------------------- small uniform (4096, FP64)
+@pytest.fixture(scope="module")
+def uniform4096(oracle_mod):
+    x = inputs.uniform(4096, seed=0)
+    return x, oracle_mod.cells(x, 0.0, 1.0, True, mode="brute")
+
+
+def test_uniform4096_plain64_all_outputs(uniform4096, oracle_mod):
+    x, o = uniform4096
+    g = gpu_run(x, 0.0, 1.0, True, "plain64", grid=(32, 1))
+    which = np.arange(len(x))
+    check_cells(g, o, oracle_mod, which, 1e-6)
+    assert np.abs(g["dens"] - 1.0 / o["vol"]).max() <= 1e-6 * (1.0 / o["vol"]).max()
+    check_gradient(g, x, o, oracle_mod, which, 0.0, 1.0, 1e-3, 1e-4)
+    ref_grid = oracle_mod.grid_density(x, 1.0 / o["vol"], 0.0, 1.0, 32, 1)
+    assert np.abs(g["grid"] - ref_grid).max() <= 1e-6 * ref_grid.max()
+    assert g["stats"]["rc"] == 0 and g["stats"]["n_faces"] == len(g["ids"])
+
+
+def test_uniform4096_filter32(uniform4096, oracle_mod):
+    x, o = uniform4096
+    g = gpu_run(x, 0.0, 1.0, True, "filter32")
+    check_cells(g, o, oracle_mod, np.arange(len(x)), 2e-5)
+    assert abs(g["vol"].sum() - 1.0) < 1e-6
+
+
+def test_uniform_fp32_inputs_both_precisions(oracle_mod):
+    x = inputs.uniform(4096 + 7, seed=5, dtype=np.float32)  # ragged last bucket
+    o = oracle_mod.cells(x.astype(np.float64), 0.0, 1.0, True, mode="certified")
+    for prec, tol in (("plain64", 1e-6), ("filter32", 2e-5)):
+        g = gpu_run(x, 0.0, 1.0, True, prec)
+        check_cells(g, o, oracle_mod, np.arange(len(x)), tol)
+
+
+# ---------------------------------------------------------------- lattices
+@pytest.mark.parametrize("kind", ["sc", "bcc"])
+def test_perturbed_lattices(kind, oracle_mod):
+    x = inputs.sc_lattice(16, perturb=1e-9, seed=0) if kind == "sc" else inputs.bcc_lattice(8, perturb=1e-9, seed=0)
+    o = oracle_mod.cells(x, 0.0, 1.0, True, mode="certified")
+    g = gpu_run(x, 0.0, 1.0, True, "plain64", grid=(32, 1))
+    which = np.arange(len(x))
+    check_cells(g, o, oracle_mod, which, 1e-6)
+    check_gradient(g, x, o, oracle_mod, which, 0.0, 1.0, 1e-3, 1e-4)
+    ref_grid = oracle_mod.grid_density(x, 1.0 / o["vol"], 0.0, 1.0, 32, 1)
+    assert np.abs(g["grid"] - ref_grid).max() <= 1e-6 * ref_grid.max()
+
+
+def test_unperturbed_sc_lattice_exact_path(oracle_mod):
+    x = inputs.sc_lattice(16)
+    o = oracle_mod.cells(x, 0.0, 1.0, True, mode="certified")
+    g = gpu_run(x, 0.0, 1.0, True, "plain64")
+    check_cells(g, o, oracle_mod, np.arange(len(x)), 1e-9)
+    assert g["stats"]["n_exact_cells"] > 0 and g["stats"]["n_exact_zero"] > 0
+    assert (np.diff(g["off"]) == 6).all()
+
+
+# ---------------------------------------------------------------- clustered, FP32
+@pytest.fixture(scope="module")
+def clustered64k(oracle_mod):
+    N = 65536
+    L = float(np.float32(100.0 * (N / 2097152) ** (1.0 / 3.0)))
+    x = inputs.clustered(N, L=L, seed=1)
+    return x, L, oracle_mod.cells(x.astype(np.float64), 0.0, L, True, mode="certified")
+
+
+@pytest.mark.parametrize("prec,tol", [("filter32", 2e-5), ("plain64", 1e-6)])
+def test_clustered64k_all_cells(clustered64k, oracle_mod, prec, tol):
+    x, L, o = clustered64k
+    g = gpu_run(x, 0.0, L, True, prec)
+    check_cells(g, o, oracle_mod, np.arange(len(x)), tol)
+    assert abs(g["vol"].sum() / L ** 3 - 1.0) < 1e-6
+    floor = 1e-3 if prec == "plain64" else 1e-1
+    check_gradient(g, x, o, oracle_mod, np.arange(len(x)), 0.0, L, floor, 1e-4)
+
+
+# ---------------------------------------------------------------- bounded box
+def test_bounded_halo_sets(oracle_mod):
+    pts, off = inputs.halo_sets(n_sets=3, nmin=300, nmax=5000, seed=6, dtype=np.float32)
+    for s in range(3):
+        x = pts[off[s]:off[s + 1]]
+        o = oracle_mod.cells(x.astype(np.float64), -1.0, 1.0, False, mode="certified")
+        for prec, tol in (("filter32", 2e-5), ("plain64", 1e-6)):
+            g = gpu_run(x, -1.0, 1.0, False, prec)
+            check_cells(g, o, oracle_mod, np.arange(len(x)), tol)
+            assert abs(g["vol"].sum() - 8.0) < 8e-6
+
+
+# ---------------------------------------------------------------- backward
+def test_backward_matches_oracle_adjoint(oracle_mod):
+    x = inputs.uniform(512, seed=9)
+    o = oracle_mod.cells(x, 0.0, 1.0, True, mode="brute")
+    gV = np.random.default_rng(1).random(len(x))
+    ref = oracle_mod.volume_adjoint(o, x, g_vol=gV, g_energy=0.7)
+    pos = torch.from_numpy(x).cuda()
+    h = vt.vt_build(pos, None, (0.0,) * 3, (1.0,) * 3, True, "plain64")
+    got = vt.backward(h, torch.from_numpy(gV), 0.7).cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-5 * scale
+
+
+# ---------------------------------------------------------------- errors
+def test_error_paths():
+    x = inputs.uniform(1000, seed=2)
+    xd = x.copy()
+    xd[10] = xd[20]
+    with pytest.raises(vt.VTError) as e:
+        gpu_run(xd, 0.0, 1.0, True, "plain64")
+    assert e.value.code == vt.VT_ERR_DUPLICATE
+    xn = x.copy()
+    xn[3, 1] = np.nan
+    with pytest.raises(vt.VTError) as e:
+        gpu_run(xn, 0.0, 1.0)
+    assert e.value.code == vt.VT_ERR_INVALID
+    xo = x.copy()
+    xo[4, 2] = 1.0  # periodic boxes are half open
+    with pytest.raises(vt.VTError) as e:
+        gpu_run(xo, 0.0, 1.0)
+    assert e.value.code == vt.VT_ERR_INVALID
+    with pytest.raises(vt.VTError) as e:
+        gpu_run(x[:2], 0.0, 1.0)
+    assert e.value.code == vt.VT_ERR_UNSUPPORTED
+    # a handle still works after failed builds
+    g = gpu_run(x, 0.0, 1.0)
+    assert abs(g["vol"].sum() - 1.0) < 1e-9
+
+
+# ---------------------------------------------------------------- full-size configurations, sampled
+def _sampled(x, L, prec, tol, oracle_mod, n_sample, seed):
+    g = gpu_run(x, 0.0, L, True, prec)
+    assert abs(g["vol"].sum() / L ** 3 - 1.0) < 1e-6
+    # neighbour symmetry over the whole set
+    N = len(x)
+    i = np.repeat(np.arange(N), np.diff(g["off"]))
+    a = i.astype(np.int64) * N + g["ids"]
+    b = g["ids"].astype(np.int64) * N + i
+    assert np.array_equal(np.sort(a), np.sort(b))
+    which = np.sort(np.random.default_rng(seed).choice(N, n_sample, replace=False))
+    o = oracle_mod.cells(x.astype(np.float64), 0.0, L, True, which=which, mode="certified")
+    check_cells(g, o, oracle_mod, which, tol)
+    return g
+
+
+def test_clustered_2M_sampled(oracle_mod):
+    x = inputs.clustered(2097152, L=100.0, seed=1)
+    g = _sampled(x, 100.0, "filter32", 2e-5, oracle_mod, 4096, 2)
+    assert g["stats"]["device_error"] == 0
