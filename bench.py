@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the Voronoi-cell hot path on GB300.
+
+One step = the whole path over one synthetic point set: vt_build (Morton key,
+radix sort, gather, bucket tree, clipping with the security-radius test and
+exact fallback, facet emission), vt_cells (volumes and the neighbour CSR),
+vt_density, vt_gradient, vt_grid_density (256^3) and vt_backward.
+
+Workload (default): 16,777,216 FP32 points, the clustered generator (60 % in
+2000 NFW halos, 25 % on filaments, 15 % uniform), seed 2, periodic box of side
+200; FP32-filtered clipping.  Inputs (201 MB) and every workspace exceed the
+129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line.  ``value`` is cells/s of the full step with inputs
+resident on the device; ``e2e`` the same through the C ABI with the positions
+copied from pinned host memory and every output copied back inside the timed
+region; ``roofline`` is the clipping kernel (the dominant one) against the
+FP32 issue peak; ``cpu_baseline`` the FP64 oracle on a bounded sample.
+``--impl reference`` times the oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Voronoi cells/sec (fwd, bwd) at 16.7M clustered pts on 1 GB300; roofline fraction"
+UNIT = "cells/s"
+
+# Algorithmic work of one cell, from the oracle on a 2048-cell sample of the workload (seed 7):
+# W = n_cert * V * 6 + V * 40 + F * 30 flops with n_cert the sites examined before the security stop,
+# V the vertices and F the facets of the final cell (see the design notes); bytes per cell of the
+# HBM-bound stages likewise.
+WORK = {
+    "clustered16M": {"n_cert": 163.2, "verts": 26.74, "faces": 15.37},
+    "clustered2M": {"n_cert": 150.0, "verts": 26.7, "faces": 15.3},
+    "uniform4096": {"n_cert": 42.4, "verts": 27.1, "faces": 15.56},
+}
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+
+
+def flops_per_cell(w):
+    return w["n_cert"] * w["verts"] * 6 + w["verts"] * 40 + w["faces"] * 30
+
+
+def workload(name):
+    from paper_1601_06429_gb300 import inputs
+
+    cache = os.path.join(tempfile.gettempdir(), "vt_bench_%s.npy" % name)
+    if name == "clustered16M":
+        L = 200.0
+        gen = lambda: inputs.clustered(16777216, L=L, seed=2)  # noqa: E731
+        desc = dict(workload="clustered 16,777,216 FP32 points, periodic box L=200, seed 2", N=16777216, L=L,
+                    grid=256)
+    elif name == "clustered2M":
+        L = 100.0
+        gen = lambda: inputs.clustered(2097152, L=L, seed=1)  # noqa: E731
+        desc = dict(workload="clustered 2,097,152 FP32 points, periodic box L=100, seed 1", N=2097152, L=L, grid=256)
+    elif name == "uniform4096":
+        L = 1.0
+        gen = lambda: inputs.uniform(4096, seed=0, dtype=np.float32)  # noqa: E731
+        desc = dict(workload="uniform 4096 FP32 points, unit periodic box, seed 0", N=4096, L=L, grid=32)
+    else:
+        raise SystemExit("unknown workload " + name)
+    if os.path.exists(cache):
+        x = np.load(cache)
+    else:
+        x = gen()
+        try:
+            np.save(cache + ".tmp.npy", x)
+            os.replace(cache + ".tmp.npy", cache)
+        except OSError:
+            pass
+    return x, desc
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while active."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if f[5 + k].strip() == "Active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, ws, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(x, L, n_sample, seed=11):
+    """The FP64 oracle (certified mode) on n_sample cells of the same point set; returns (cells/s, info)."""
+    import oracle
+
+    oracle.build()
+    which = np.sort(np.random.default_rng(seed).choice(len(x), n_sample, replace=False))
+    x64 = x.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.cells(x64, 0.0, L, True, which=which, mode="certified")
+    t1 = time.perf_counter()
+    cores = os.cpu_count()
+    return n_sample / (t1 - t0), dict(cores=cores, seconds=t1 - t0,
+                                      sample="%d random cells of the same point set (k-d tree over all %d points "
+                                             "built inside the timed call), certified mode, FP64" % (n_sample, len(x)))
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup(args)
+    if rank != 0:
+        return 0
+    x, desc = workload(args.workload)
+    rates = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        r, info = cpu_oracle_rate(x, desc["L"], args.ref_sample, seed=100 + k)
+        if k >= args.warmup:
+            rates.append(r)
+    value = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * desc["N"] / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {k: v for k, v in desc.items() if k in ("workload",)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1601_06429_gb300 import binding as vt
+    from paper_1601_06429_gb300.build import build
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build()
+    barrier(ws)
+    vt.load_library()
+    x, desc = workload(args.workload)
+    N, L, G = desc["N"], desc["L"], desc["grid"]
+    box = ((0.0,) * 3, (L,) * 3)
+    stream = torch.cuda.current_stream(dev)
+    xd = torch.from_numpy(x).to(dev)
+    w = torch.from_numpy(np.random.default_rng(4).random(N).astype(np.float32)).to(dev)  # dL/dV weights
+    vol = torch.empty(N, dtype=torch.float32, device=dev)
+    dens = torch.empty(N, dtype=torch.float32, device=dev)
+    grad = torch.empty(N, 3, dtype=torch.float32, device=dev)
+    off = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    ids = torch.empty(24 * N, dtype=torch.int32, device=dev)
+    grid = torch.empty(G, G, G, dtype=torch.float32, device=dev)
+    dpos = torch.empty(N, 3, dtype=torch.float32, device=dev)
+    stats = []
+
+    def step(pos_dev):
+        nonlocal ids
+        h = vt.vt_build(pos_dev, None, box[0], box[1], True, args.precision)
+        nnz = vt.vt_cells(h)
+        if nnz > ids.numel():
+            ids = torch.empty(int(nnz * 1.2), dtype=torch.int32, device=dev)
+        vt.vt_cells(h, vol, off, ids)
+        vt.vt_density(h, dens)
+        vt.vt_gradient(h, grad)
+        vt.vt_grid_density(h, G, 1, grid)
+        vt.vt_backward(h, w, 0.0, dpos)
+        st = vt.vt_status(h)
+        vt.vt_destroy(h)
+        if st["rc"] != 0:
+            raise RuntimeError("device error %d" % st["rc"])
+        stats.append(st)
+        return nnz
+
+    # ---------------- device-resident inputs
+    for _ in range(args.warmup):
+        step(xd)
+    stats.clear()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = Clocks(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        nnz = step(xd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    barrier(ws)
+    t_ms = max_over_ranks(t_ms, ws, dev)
+    ms_step = t_ms / args.steps
+    value = ws * N * args.steps / (t_ms / 1000.0)
+    clip_ms = statistics.mean(s["t_clip_ms"] for s in stats)
+    sort_ms = statistics.mean(s["t_sort_ms"] for s in stats)
+    launches = sum(s["n_launches"] for s in stats)
+
+    # ---------------- end to end through the ABI with host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    outs_h = dict(vol=torch.empty(N, dtype=torch.float32).pin_memory(),
+                  dens=torch.empty(N, dtype=torch.float32).pin_memory(),
+                  grad=torch.empty(N, 3, dtype=torch.float32).pin_memory(),
+                  off=torch.empty(N + 1, dtype=torch.int64).pin_memory(),
+                  grid=torch.empty(G, G, G, dtype=torch.float32).pin_memory(),
+                  dpos=torch.empty(N, 3, dtype=torch.float32).pin_memory())
+    ids_h = torch.empty(ids.numel(), dtype=torch.int32).pin_memory()
+    xd2 = torch.empty_like(xd)
+
+    def e2e_step():
+        xd2.copy_(xh, non_blocking=True)
+        n = step(xd2)
+        outs_h["vol"].copy_(vol, non_blocking=True)
+        outs_h["dens"].copy_(dens, non_blocking=True)
+        outs_h["grad"].copy_(grad, non_blocking=True)
+        outs_h["off"].copy_(off, non_blocking=True)
+        outs_h["grid"].copy_(grid, non_blocking=True)
+        outs_h["dpos"].copy_(dpos, non_blocking=True)
+        ids_h[:n].copy_(ids[:n], non_blocking=True)
+        return n
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0.record(stream)
+    for _ in range(args.steps):
+        n = e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    e2e_value = ws * N * args.steps / (te_ms / 1000.0)
+    h2d = N * 12
+    d2h = N * 4 + N * 4 + N * 12 + (N + 1) * 8 + G ** 3 * 4 + N * 12 + n * 4
+
+    # ---------------- roofline of the clipping kernel (FP32 issue bound)
+    wk = WORK.get(args.workload, WORK["clustered16M"])
+    fpc = flops_per_cell(wk)
+    achieved = fpc * N / (clip_ms / 1000.0) / 1e12
+    peak_mhz = 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    if args.precision == "plain64":
+        peak = peak / 64.0
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "filter32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": desc["workload"], "precision": args.precision, "grid": "%d^3" % G,
+                       "parallelism": "replicas" if ws > 1 else "1 GPU",
+                       "l2": "inputs and workspaces larger than L2 (no flush)"},
+            "fwd_bwd_breakdown_ms": {"build_sort_tree": sort_ms, "build_clip": clip_ms,
+                                     "rest_of_step": ms_step - sort_ms - clip_ms},
+            "faces_per_cell": nnz / N,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_clip (clipping, security test, facet emission)",
+                         "work": "%.0f algorithmic flops/cell x %d cells per launch" % (fpc, N),
+                         "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"},
+            "clocks": clocks,
+            "device_counters": {k: stats[-1][k] for k in ("n_cut", "n_tested", "n_passes", "n_fp64_fallbacks",
+                                                          "n_exact_cells", "n_exact_preds", "max_faces")}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, info = cpu_oracle_rate(x, L, args.cpu_sample)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                                "sample": info["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="clustered16M")
+    ap.add_argument("--precision", choices=["filter32", "plain64"], default="filter32")
+    ap.add_argument("--cpu-sample", type=int, default=8192)
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

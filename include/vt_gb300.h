@@ -65,9 +65,10 @@ extern "C" {
 typedef struct vt_params {
     int precision;  /* VT_PLAIN64 or VT_FILTER32 (default VT_FILTER32) */
     int k_target;   /* particles aimed for in a cell's first candidate pass (default 40) */
-    int max_passes; /* candidate radius passes per cell before VT_ERR_SECURITY (default 24) */
+    int max_passes; /* candidate radius passes per cell before VT_ERR_SECURITY (default 1000) */
     int face_pool;  /* facet records reserved per particle (default 24; grown on demand) */
-    int reserved[4];
+    int reserved[4]; /* [0]: candidate pass sizing, 0 = radius doubling up to 2R (default), 1 = also limited
+                        by the density seen so far; others must be 0 */
 } vt_params;
 
 typedef struct vt_stats {
@@ -83,7 +84,11 @@ typedef struct vt_stats {
     int64_t max_faces;        /* largest facet count of a cell */
     int32_t device_error;     /* first VT_ERR_* recorded on the device, or VT_OK */
     int32_t error_particle;   /* an input index that raised it, or -1 */
-    int64_t reserved[6];
+    int64_t n_launches;       /* CUDA kernels launched through this handle so far */
+    double t_sort_ms;         /* device time of vt_build's key, sort, gather and tree kernels (CUDA events) */
+    double t_clip_ms;         /* device time of vt_build's clipping kernels, last attempt (CUDA events) */
+    int64_t reserved[3];      /* diagnostics: [0] internal detail of device_error, [1] candidate collections,
+                                 [2] candidates collected */
 } vt_stats;
 
 typedef struct vt_handle_s *vt_handle;
@@ -158,6 +163,14 @@ int vt_backward(vt_handle h, const void *dL_dV, double dL_dE, void *dL_dpos);
 
 /* vt_status -- counters and the sticky device error; synchronises the stream. */
 int vt_status(vt_handle h, vt_stats *out);
+
+/*
+ * vt_last_error_detail -- diagnostics of the last vt_build on the calling host thread that failed with a
+ * device-detected error: returns an internal reason code (0 if none; for VT_ERR_CAPACITY: -101 planes,
+ * -102 vertices, -103 boundary edges, -104 candidates, -105 search stack) and stores in *particle (if not
+ * NULL) an input index whose cell raised it, or -1.  Not part of the paper's method.
+ */
+int vt_last_error_detail(int *particle);
 
 /* vt_error_string -- static description of a VT_* code. */
 const char *vt_error_string(int code);

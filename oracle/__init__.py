@@ -56,7 +56,7 @@ def _load():
         P = ctypes.c_void_p
         i64 = ctypes.c_int64
         i32 = ctypes.c_int
-        lib.oracle_cells.argtypes = [i64, P, P, P, i32, P, i64, i32, i32] + [P] * 14 + [i32]
+        lib.oracle_cells.argtypes = [i64, P, P, P, i32, P, i64, i32, i32] + [P] * 15 + [i32]
         lib.oracle_cells.restype = i32
         lib.oracle_insphere_side.argtypes = [P, P, P, P, P, i32]
         lib.oracle_insphere_side.restype = i32
@@ -87,7 +87,7 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     them from a k-d tree in radius passes (same result).
 
     Returns a dict with per-cell ``vol``, ``cen`` (cell centroid),
-    ``mom2`` (integral of |y - x_i|^2 over the cell), ``nface``, ``nvert``,
+    ``mom2`` (integral of |y - x_i|^2 over the cell), ``rmax`` (largest vertex distance), ``nface``, ``nvert``,
     ``nedge``, ``ntest`` (planes examined) and ``ncut`` (planes that cut),
     the faces in CSR form (``face_off``, ``f_nbr`` (neighbour id, -1-w for
     box wall w), ``f_shift`` (periodic image), ``f_area``, ``f_cen``,
@@ -107,6 +107,7 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     vol = np.zeros(n)
     cen = np.zeros((n, 3))
     mom2 = np.zeros(n)
+    rmax = np.zeros(n)
     nface = np.zeros(n, np.int32)
     nvert = np.zeros(n, np.int32)
     nedge = np.zeros(n, np.int32)
@@ -120,7 +121,7 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     counters = np.zeros(4, np.int64)
     rc = lib.oracle_cells(N, _ptr(pos), _ptr(lo), _ptr(hi), int(bool(periodic)), _ptr(wh), n,
                           {"brute": 0, "certified": 1}[mode], face_cap,
-                          _ptr(vol), _ptr(cen), _ptr(mom2), _ptr(nface), _ptr(nvert), _ptr(nedge),
+                          _ptr(vol), _ptr(cen), _ptr(mom2), _ptr(rmax), _ptr(nface), _ptr(nvert), _ptr(nedge),
                           _ptr(ntest), _ptr(ncut), _ptr(f_nbr), _ptr(f_shift), _ptr(f_area), _ptr(f_cen),
                           _ptr(f_dist), _ptr(counters), int(nthreads))
     if rc != 0:
@@ -129,7 +130,7 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     face_off = np.zeros(n + 1, np.int64)
     face_off[1:] = np.cumsum(nf)
     sel = (np.arange(face_cap)[None, :] < nf[:, None]).reshape(-1)
-    return dict(which=wh if wh is not None else np.arange(N, dtype=np.int64), vol=vol, cen=cen, mom2=mom2,
+    return dict(which=wh if wh is not None else np.arange(N, dtype=np.int64), vol=vol, cen=cen, mom2=mom2, rmax=rmax,
                 nface=nface, nvert=nvert, nedge=nedge, ntest=ntest, ncut=ncut, face_off=face_off,
                 f_nbr=f_nbr[sel], f_shift=f_shift[sel], f_area=f_area[sel], f_cen=f_cen[sel],
                 f_dist=f_dist[sel], counters=counters)

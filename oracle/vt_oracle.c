@@ -598,7 +598,7 @@ static void kd_query(const kdtree *t, int64_t i, const int s[3], double r_lo2, d
 /* per-cell driver                                                      */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    double vol, cen[3], mom2;
+    double vol, cen[3], mom2, rmax;
     int nface, nvert, nedge;
     int64_t n_tested, n_cut;
 } cellout;
@@ -785,6 +785,12 @@ static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int3
     co->vol = vol;
     for (int c = 0; c < 3; c++) co->cen[c] = (vol > 0 ? cz[c] / vol : 0.0) + pb->x[3 * cw->i + c];
     co->mom2 = m2;
+    co->rmax = 0.0;
+    for (int k = 0; k < cw->nv; k++) {
+        const double *y = cw->v[k].y;
+        double r = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
+        if (r > co->rmax) co->rmax = r;
+    }
     co->nface = nf;
     co->nvert = cw->nv;
     co->nedge = nedge2 / 2;
@@ -802,7 +808,8 @@ static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int3
  *   cells     particle ids to compute (NULL: all, n_cells = N)
  *   mode      0 brute force over all 27N-1 images, 1 certified k-d tree
  *   face_cap  face slots per listed cell
- * per listed cell k:  vol[k], cen[3k..], mom2[k] = integral |y - x_i|^2,
+ * per listed cell k:  vol[k], cen[3k..], mom2[k] = integral |y - x_i|^2, rmax[k] = largest vertex
+ *   distance from x_i,
  *   nface[k] (< 0: error code), nvert[k], nedge[k], ntest[k] (planes
  *   examined), ncut[k] (planes that cut);
  * face slots [k*face_cap, k*face_cap + nface[k]):  f_nbr (neighbour id, or
@@ -813,7 +820,8 @@ static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int3
  */
 int oracle_cells(int64_t N, const double *pos, const double *box_lo, const double *box_hi, int periodic,
                  const int64_t *cells, int64_t n_cells, int mode, int face_cap, double *vol, double *cen,
-                 double *mom2, int32_t *nface, int32_t *nvert, int32_t *nedge, int64_t *ntest, int64_t *ncut,
+                 double *mom2, double *rmax, int32_t *nface, int32_t *nvert, int32_t *nedge, int64_t *ntest,
+                 int64_t *ncut,
                  int64_t *f_nbr, int32_t *f_shift, double *f_area, double *f_cen, double *f_dist,
                  int64_t *counters, int nthreads) {
     problem pb;
@@ -858,13 +866,13 @@ int oracle_cells(int64_t N, const double *pos, const double *box_lo, const doubl
             ntest[k] = cw.n_tested; ncut[k] = cw.n_cut;
             if (rc != 0) {
                 tot_err++;
-                nface[k] = rc; vol[k] = NAN; mom2[k] = NAN;
+                nface[k] = rc; vol[k] = NAN; mom2[k] = NAN; rmax[k] = NAN;
                 for (int c = 0; c < 3; c++) cen[3 * k + c] = NAN;
                 nvert[k] = nedge[k] = 0;
 #pragma omp critical
                 { if (!first_err) first_err = rc; }
             } else {
-                nface[k] = co.nface; vol[k] = co.vol; mom2[k] = co.mom2;
+                nface[k] = co.nface; vol[k] = co.vol; mom2[k] = co.mom2; rmax[k] = co.rmax;
                 for (int c = 0; c < 3; c++) cen[3 * k + c] = co.cen[c];
                 nvert[k] = co.nvert; nedge[k] = co.nedge;
             }

@@ -40,17 +40,25 @@ class vt_stats(ctypes.Structure):
                 ("n_tested", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_fp64_fallbacks", ctypes.c_int64),
                 ("n_exact_cells", ctypes.c_int64), ("n_exact_preds", ctypes.c_int64),
                 ("n_exact_zero", ctypes.c_int64), ("max_faces", ctypes.c_int64), ("device_error", ctypes.c_int32),
-                ("error_particle", ctypes.c_int32), ("reserved", ctypes.c_int64 * 6)]
+                ("error_particle", ctypes.c_int32), ("n_launches", ctypes.c_int64), ("t_sort_ms", ctypes.c_double),
+                ("t_clip_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d["error_detail"] = int(self.reserved[0])
+        d["n_collect"] = int(self.reserved[1])
+        d["n_collected"] = int(self.reserved[2])
+        return d
 
 
 class VTError(RuntimeError):
-    def __init__(self, code, where=""):
+    def __init__(self, code, where="", detail=0, particle=-1):
         self.code = int(code)
+        self.detail = int(detail)
+        self.particle = int(particle)
         msg = error_string(code)
-        super().__init__("%s: %s (%d)" % (where or "vt", msg, code))
+        extra = " [detail %d, particle %d]" % (detail, particle) if detail else ""
+        super().__init__("%s: %s (%d)%s" % (where or "vt", msg, code, extra))
 
 
 _lib = None
@@ -85,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_backward.restype = i32
     lib.vt_status.argtypes = [P, ctypes.POINTER(vt_stats)]
     lib.vt_status.restype = i32
+    lib.vt_last_error_detail.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    lib.vt_last_error_detail.restype = i32
     lib.vt_error_string.argtypes = [i32]
     lib.vt_error_string.restype = ctypes.c_char_p
     lib.vt_destroy.argtypes = [P]
@@ -123,6 +133,13 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def vt_last_error_detail():
+    """(reason, particle) of the last failed vt_build on this thread."""
+    part = ctypes.c_int(-1)
+    det = load_library().vt_last_error_detail(ctypes.byref(part))
+    return int(det), int(part.value)
+
+
 def vt_default_params() -> vt_params:
     p = vt_params()
     _check(load_library().vt_default_params(ctypes.byref(p)), "vt_default_params")
@@ -147,7 +164,7 @@ class Handle:
 
 
 def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), periodic=True, precision="filter32",
-             k_target=40, max_passes=24, face_pool=24, stream=None) -> Handle:
+             k_target=40, max_passes=1000, face_pool=24, stream=None, radius_policy=0) -> Handle:
     """Voronoi cells of all particles; ``pos`` is a CUDA [N,3] float32/float64 tensor."""
     import torch
 
@@ -165,6 +182,7 @@ def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), per
     p.k_target = int(k_target)
     p.max_passes = int(max_passes)
     p.face_pool = int(face_pool)
+    p.reserved[0] = int(radius_policy)
     lo = (ctypes.c_double * 3)(*[float(v) for v in (box_lo if hasattr(box_lo, "__len__") else (box_lo,) * 3)])
     hi = (ctypes.c_double * 3)(*[float(v) for v in (box_hi if hasattr(box_hi, "__len__") else (box_hi,) * 3)])
     h = ctypes.c_void_p()
@@ -172,7 +190,10 @@ def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), per
     with torch.cuda.device(pos.device):
         rc = lib.vt_build(ctypes.byref(h), _ptr(pos), dt, _ptr(mass), pos.shape[0], lo, hi, int(bool(periodic)),
                           ctypes.byref(p), _stream_ptr(stream))
-    _check(rc, "vt_build")
+    if rc != VT_OK:
+        part = ctypes.c_int(-1)
+        det = lib.vt_last_error_detail(ctypes.byref(part))
+        raise VTError(rc, "vt_build", det, part.value)
     return Handle(h, pos.shape[0], pos.dtype, pos.device, stream)
 
 

@@ -16,6 +16,10 @@ namespace {
 
 constexpr int RC_POOL_HOST = 1001;  // device code for "facet pool too small" (the host grows it)
 
+// internal detail of the last failed vt_build on this thread (diagnostics)
+thread_local int g_last_detail = 0;
+thread_local int g_last_particle = -1;
+
 struct Alloc {
     bool failed = false;
     template <typename T>
@@ -33,6 +37,8 @@ struct Alloc {
 
 void free_handle(vt_handle h) {
     if (!h) return;
+    for (int k = 0; k < 4; k++)
+        if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     void* ptrs[] = {h->spos, h->perm, h->inv, h->tree_mem, h->cell, h->face_start, h->face_count, h->cstat,
                     h->exact_list, h->dens_sorted, h->faces, h->xws, h->tmp, h->nbr_off_cache, h->dstat,
                     h->keys, h->keys_alt, h->vals_alt, h->cnt_in};
@@ -55,6 +61,7 @@ ClipArgs clip_args(vt_handle h) {
     a.tree = h->tree;
     a.k_target = h->prm.k_target;
     a.max_passes = h->prm.max_passes;
+    a.radius_policy = h->prm.reserved[0];
     a.cell = h->cell;
     a.face_start = h->face_start;
     a.face_count = h->face_count;
@@ -81,14 +88,18 @@ int run_clip(vt_handle h) {
         rc = cuda_rc(cudaStreamSynchronize(s));
         if (rc) return rc;
         ClipArgs a = clip_args(h);
-        launch_clip(a, h->dtype, h->precision, h->sm_count, s);
-        launch_clip_exact(a, h->dtype, h->sm_count, s);
+        cudaEventRecord(h->ev[2], s);
+        h->n_launches += launch_clip(a, h->dtype, h->precision, h->sm_count, s);
+        h->n_launches += launch_clip_exact(a, h->dtype, h->sm_count, s);
+        cudaEventRecord(h->ev[3], s);
         rc = cuda_rc(cudaGetLastError());
         if (rc) return rc;
         rc = cuda_rc(cudaMemcpyAsync(&h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         if (rc) return rc;
         rc = cuda_rc(cudaStreamSynchronize(s));
         if (rc) return rc;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]) == cudaSuccess) h->t_clip_ms = ms;
         if (h->hstat.error != RC_POOL_HOST) return h->hstat.error;
         // facet pool too small: grow it and redo the cells
         uint64_t need = h->hstat.face_next + (uint64_t)h->N * 4;
@@ -110,7 +121,7 @@ __global__ void k_set_i64(int64_t* p, int64_t v) { *p = v; }
 
 int ensure_density(vt_handle h) {
     if (h->dens_ready) return VT_OK;
-    launch_density(h->cell, h->spos, h->dtype, h->perm, h->N, h->dens_sorted, nullptr, h->stream);
+    h->n_launches += launch_density(h->cell, h->spos, h->dtype, h->perm, h->N, h->dens_sorted, nullptr, h->stream);
     h->dens_ready = 1;
     return cuda_rc(cudaGetLastError());
 }
@@ -124,7 +135,7 @@ int vt_default_params(vt_params* p) {
     memset(p, 0, sizeof(*p));
     p->precision = VT_FILTER32;
     p->k_target = 40;
-    p->max_passes = 24;
+    p->max_passes = 1000;
     p->face_pool = 24;
     return VT_OK;
 }
@@ -139,7 +150,8 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     vt_default_params(&prm);
     if (p) prm = *p;
     if (prm.precision != VT_PLAIN64 && prm.precision != VT_FILTER32) return VT_ERR_INVALID;
-    if (prm.k_target < 8 || prm.k_target > 120 || prm.max_passes < 1 || prm.max_passes > 1000 || prm.face_pool < 1 ||
+    if (prm.reserved[0] < 0 || prm.reserved[0] > 1) return VT_ERR_INVALID;
+    if (prm.k_target < 8 || prm.k_target > 120 || prm.max_passes < 1 || prm.max_passes > 100000 || prm.face_pool < 1 ||
         prm.face_pool > 128)
         return VT_ERR_INVALID;
     Geometry geo;
@@ -199,6 +211,12 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     h->tmp_bytes = tb > sb ? tb : sb;
     h->tmp = A.get<unsigned char>(h->tmp_bytes);
     h->dstat = A.get<DevStatus>(1);
+    for (int k = 0; k < 4; k++)
+        if (cudaEventCreate(&h->ev[k]) != cudaSuccess) {
+            cudaGetLastError();
+            h->ev[k] = nullptr;
+            A.failed = true;
+        }
     if (A.failed) {
         free_handle(h);
         return VT_ERR_OOM;
@@ -207,20 +225,35 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     memset(&h->hstat, 0, sizeof(h->hstat));
     int rc = cuda_rc(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), s));
     if (!rc) {
-        launch_key(pos, dtype, N, geo, h->keys, h->perm, h->dstat, s);
-        radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48, h->tmp, s);
-        launch_gather(pos, mass, dtype, h->perm, N, h->spos, h->inv, s);
-        launch_tree(h->spos, dtype, N, h->tree, s);
+        cudaEventRecord(h->ev[0], s);
+        h->n_launches += launch_key(pos, dtype, N, geo, h->keys, h->perm, h->dstat, s);
+        h->n_launches += radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48, h->tmp, s);
+        h->n_launches += launch_gather(pos, mass, dtype, h->perm, N, h->spos, h->inv, s);
+        h->n_launches += launch_tree(h->spos, dtype, N, h->tree, s);
+        cudaEventRecord(h->ev[1], s);
         rc = cuda_rc(cudaGetLastError());
     }
     if (!rc) rc = cuda_rc(cudaMemcpyAsync(&h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     if (!rc) rc = cuda_rc(cudaStreamSynchronize(s));
+    if (!rc) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) == cudaSuccess) h->t_sort_ms = ms;
+    }
     if (!rc && h->hstat.invalid_input) rc = VT_ERR_INVALID;
     if (!rc) rc = run_clip(h);
     if (rc) {
+        g_last_detail = h->hstat.error_detail;
+        g_last_particle = -1;
+        if (h->hstat.error && h->hstat.error_cell >= 0 && h->hstat.error_cell < N && h->perm) {
+            uint32_t pi = 0;
+            if (cudaMemcpy(&pi, h->perm + h->hstat.error_cell, sizeof(pi), cudaMemcpyDeviceToHost) == cudaSuccess)
+                g_last_particle = (int)pi;
+        }
         free_handle(h);
         return rc;
     }
+    g_last_detail = 0;
+    g_last_particle = -1;
     h->n_faces = (int64_t)h->hstat.n_faces;
     *out = h;
     return VT_OK;
@@ -230,7 +263,7 @@ int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t*
     if (!h) return VT_ERR_INVALID;
     cudaStream_t s = h->stream;
     if (n_faces_out) *n_faces_out = h->n_faces;
-    if (vol) launch_out_vol(h->cell, h->perm, h->N, vol, h->dtype, s);
+    if (vol) h->n_launches += launch_out_vol(h->cell, h->perm, h->N, vol, h->dtype, s);
     if (nbr_off || nbr_id) {
         int64_t* off = nbr_off;
         if (!off) {
@@ -241,17 +274,19 @@ int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t*
             }
             off = h->nbr_off_cache;
         }
-        launch_nbr_count(h->face_count, h->inv, h->N, h->cnt_in, s);
-        scan_u16_i64(h->cnt_in, off, h->N, h->tmp, s);
+        h->n_launches += launch_nbr_count(h->face_count, h->inv, h->N, h->cnt_in, s);
+        h->n_launches += scan_u16_i64(h->cnt_in, off, h->N, h->tmp, s);
         k_set_i64<<<1, 1, 0, s>>>(off + h->N, h->n_faces);
-        if (nbr_id) launch_nbr_emit(h->faces, h->face_start, h->face_count, h->perm, h->inv, off, h->N, nbr_id, s);
+        h->n_launches += 1;
+        if (nbr_id)
+            h->n_launches += launch_nbr_emit(h->faces, h->face_start, h->face_count, h->perm, h->inv, off, h->N, nbr_id, s);
     }
     return cuda_rc(cudaGetLastError());
 }
 
 int vt_density(vt_handle h, void* dens) {
     if (!h || !dens) return VT_ERR_INVALID;
-    launch_density(h->cell, h->spos, h->dtype, h->perm, h->N, h->dens_sorted, dens, h->stream);
+    h->n_launches += launch_density(h->cell, h->spos, h->dtype, h->perm, h->N, h->dens_sorted, dens, h->stream);
     h->dens_ready = 1;
     return cuda_rc(cudaGetLastError());
 }
@@ -260,7 +295,7 @@ int vt_gradient(vt_handle h, void* grad) {
     if (!h || !grad) return VT_ERR_INVALID;
     int rc = ensure_density(h);
     if (rc) return rc;
-    launch_gradient(h->faces, h->face_start, h->face_count, h->dens_sorted, h->perm, h->N, grad, h->dtype, h->stream);
+    h->n_launches += launch_gradient(h->faces, h->face_start, h->face_count, h->dens_sorted, h->perm, h->N, grad, h->dtype, h->stream);
     return cuda_rc(cudaGetLastError());
 }
 
@@ -269,14 +304,14 @@ int vt_grid_density(vt_handle h, int G, int S, void* grid) {
     if ((int64_t)G * G * G > ((int64_t)1 << 34)) return VT_ERR_INVALID;
     int rc = ensure_density(h);
     if (rc) return rc;
-    launch_grid(h->spos, h->dtype, h->N, h->geo, h->tree, h->dens_sorted, h->perm, G, S, grid, h->dstat, h->sm_count,
-                h->stream);
+    h->n_launches += launch_grid(h->spos, h->dtype, h->N, h->geo, h->faces, h->face_start, h->face_count, h->keys,
+                                 h->dens_sorted, h->perm, G, S, grid, h->dstat, h->stream);
     return cuda_rc(cudaGetLastError());
 }
 
 int vt_backward(vt_handle h, const void* dL_dV, double dL_dE, void* dL_dpos) {
     if (!h || !dL_dpos || !isfinite(dL_dE)) return VT_ERR_INVALID;
-    launch_backward(h->faces, h->face_start, h->face_count, h->cell, h->spos, h->dtype, h->perm, h->inv, h->N, dL_dV,
+    h->n_launches += launch_backward(h->faces, h->face_start, h->face_count, h->cell, h->spos, h->dtype, h->perm, h->inv, h->N, dL_dV,
                     dL_dE, dL_dpos, h->stream);
     return cuda_rc(cudaGetLastError());
 }
@@ -299,6 +334,12 @@ int vt_status(vt_handle h, vt_stats* out) {
     out->n_exact_zero = (int64_t)d.n_exact_zero;
     out->max_faces = (int64_t)d.max_faces;
     out->device_error = d.error;
+    out->n_launches = h->n_launches;
+    out->t_sort_ms = h->t_sort_ms;
+    out->t_clip_ms = h->t_clip_ms;
+    out->reserved[0] = d.error_detail;
+    out->reserved[1] = (int64_t)d.n_collect;
+    out->reserved[2] = (int64_t)d.n_collected;
     out->error_particle = -1;
     if (d.error && d.error_cell >= 0 && d.error_cell < h->N) {
         uint32_t pi = 0;
@@ -306,6 +347,11 @@ int vt_status(vt_handle h, vt_stats* out) {
             out->error_particle = (int32_t)pi;
     }
     return d.error ? d.error : VT_OK;
+}
+
+int vt_last_error_detail(int* particle) {
+    if (particle) *particle = g_last_particle;
+    return g_last_detail;
 }
 
 const char* vt_error_string(int code) {

@@ -8,13 +8,15 @@ void launch_clip_f64(const ClipArgs& a, int precision, int sm_count, cudaStream_
 
 size_t exact_ws_doubles_per_warp() { return EXACT_WS; }
 
-void launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s) {
+int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s) {
     if (dtype == VT_F32) launch_clip_f32(a, precision, sm_count, s);
     else launch_clip_f64(a, precision, sm_count, s);
+    return 1;
 }
 
-void launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s) {
+int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s) {
     if (dtype == VT_F32) launch_one<float4, double, true>(a, sm_count, s);
     else launch_one<dpt4, double, true>(a, sm_count, s);
+    return 1;
 }
 }  // namespace vt

@@ -35,6 +35,22 @@
 namespace vt {
 
 constexpr int CLIP_WARPS = 4;
+constexpr int HIST_BINS = 64;
+
+// Per-cell capacities.  TP = vertex slots per lane.  The fast kernels use Cap<4> (128 vertices, 128 planes with
+// 8-bit ids); cells that overflow them, and cells whose FP64 tests stay undecided, are redone by the exact
+// kernel with Cap<16> (512 vertices, 512 planes with 10-bit ids).
+template <int TP>
+struct Cap {
+    static constexpr int TPL = TP;
+    static constexpr int MAXT = 32 * TP;
+    static constexpr int IDB = TP <= 4 ? 8 : 10;          // bits of a plane id in a packed triangle
+    static constexpr int MAXP = TP <= 4 ? 128 : 512;
+    static constexpr uint32_t IDM = (1u << IDB) - 1u;
+    static constexpr int SB = TP <= 4 ? 7 : 9;            // bits of a vertex slot
+    static constexpr int CAND = TP <= 4 ? 128 : 256;      // candidates per radius pass
+    static constexpr int STACK = TP <= 4 ? STACK_CAP : 4 * STACK_CAP;
+};
 constexpr int CHUNK = 4;
 constexpr int EXACT_WS = 12288;  // doubles per warp for expansion arithmetic
 
@@ -51,23 +67,34 @@ template <> struct Stor<float4> { typedef float T; };
 template <> struct Stor<dpt4> { typedef double T; };
 
 // ------------------------------------------------------------------ shared memory
-template <typename CT>
+template <typename CT, int TP>
 struct WarpSmem {
-    CT pnx[MAXP], pny[MAXP], pnz[MAXP], ph[MAXP], pnrm[MAXP];
-    uint32_t psrc[MAXP];
-    uint8_t pcode[MAXP];  // 0..26 image shift code, 27+w box wall w
+    typedef Cap<TP> K;
+    // planes that have cut the cell: n.y <= h with |n| = nrm, source particle and image shift
+    CT pnx[K::MAXP], pny[K::MAXP], pnz[K::MAXP], ph[K::MAXP], pnrm[K::MAXP];
+    uint32_t psrc[K::MAXP];
+    uint8_t pcode[K::MAXP];  // 0..26 image shift code, 27+w box wall w
+    // vertices = triangles of the dual triangulation: packed plane ids, position, error bound, R^2 bound
+    uint32_t tid[K::MAXT];
+    uint32_t tadj[K::MAXT];  // neighbour slot across edge k (k = 0: a->b, 1: b->c, 2: c->a), 10 bits each
+    CT tx[K::MAXT], ty[K::MAXT], tz[K::MAXT], tev[K::MAXT], trr[K::MAXT];
     union {
-        unsigned long long cand[CAND_CAP];
         struct {
-            uint32_t tid[MAXT];
-            CT tx[MAXT], ty[MAXT], tz[MAXT];
-            uint32_t hash[HASH_SZ];
-            uint32_t first[MAXP];
+            unsigned long long key[K::CAND];  // (|d|^2 as float bits) << 32 | slot
+            CT dx[K::CAND], dy[K::CAND], dz[K::CAND];
+            uint32_t j[K::CAND];
+            uint8_t code[K::CAND];
+        } cd;
+        struct {
+            uint32_t first[K::MAXP];
         } em;
     } u;
-    uint16_t edges[3 * MAXT];
-    uint16_t bnd[MAXT];
-    uint32_t stack[STACK_CAP];
+    uint32_t bnd[K::MAXT];       // boundary records of a cut: x, y, kept neighbour slot, its edge index
+    uint16_t lnk_s[K::MAXP];     // new triangle whose boundary edge starts at plane x
+    uint16_t lnk_e[K::MAXP];     // new triangle whose boundary edge ends at plane y
+    uint32_t stack[K::STACK];
+    uint32_t hist[HIST_BINS];  // radial histogram of an overflowing candidate pass
+    uint16_t live[K::MAXP];    // plane-id compaction
 };
 
 // ------------------------------------------------------------------ small helpers
@@ -145,6 +172,18 @@ __device__ __forceinline__ double dcomp_shift_d(double xj, double xi, double L, 
 template <typename CT> __device__ __forceinline__ CT f_fma(CT a, CT b, CT c);
 template <> __device__ __forceinline__ float f_fma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 template <> __device__ __forceinline__ double f_fma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// bit pattern of a non-negative value (order preserving), and back
+template <typename CT> __device__ __forceinline__ unsigned long long fbits(CT v);
+template <> __device__ __forceinline__ unsigned long long fbits<float>(float v) { return __float_as_uint(v); }
+template <> __device__ __forceinline__ unsigned long long fbits<double>(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+template <typename CT> __device__ __forceinline__ CT fromfbits(unsigned long long b);
+template <> __device__ __forceinline__ float fromfbits<float>(unsigned long long b) { return __uint_as_float((uint32_t)b); }
+template <> __device__ __forceinline__ double fromfbits<double>(unsigned long long b) {
+    return __longlong_as_double((long long)b);
+}
 
 // displacement of particle j seen from i in precision CT, and the periodic shift used
 template <typename P, typename CT> struct DispF;
@@ -318,7 +357,7 @@ __device__ void x_row(XWork& w, Xe row[4], const P* spos, const Geometry& g, uin
 
 // +1: vertex of (a,b,c) strictly beyond plane j; -1: strictly inside; 0: on it.  *ovf on workspace overflow.
 template <typename P>
-__device__ int exact_side(double* ws, const P* spos, const Geometry& g, uint32_t self, PRef a, PRef b, PRef c, PRef j,
+__device__ __noinline__ int exact_side(double* ws, const P* spos, const Geometry& g, uint32_t self, PRef a, PRef b, PRef c, PRef j,
                           bool* ovf) {
     XWork w;
     w.base = ws; w.used = 0; w.cap = EXACT_WS; w.overflow = false;
@@ -394,7 +433,7 @@ __device__ void plane64(const P* spos, const Geometry& g, uint32_t self, PRef r,
 }
 
 template <typename P>
-__device__ int side64(const P* spos, const Geometry& g, uint32_t self, PRef a, PRef b, PRef c, PRef j) {
+__device__ __noinline__ int side64(const P* spos, const Geometry& g, uint32_t self, PRef a, PRef b, PRef c, PRef j) {
     double ax, ay, az, ah, an, bx, by, bz, bh, bn, cx, cy, cz, chh, cn, jx, jy, jz, jh, jn;
     plane64<P>(spos, g, self, a, ax, ay, az, ah, an);
     plane64<P>(spos, g, self, b, bx, by, bz, bh, bn);
@@ -410,200 +449,353 @@ __device__ int side64(const P* spos, const Geometry& g, uint32_t self, PRef a, P
 }
 
 // ------------------------------------------------------------------ per-cell state
-template <typename CT>
-struct Tris {
-    uint32_t id[TPL];
-    CT x[TPL], y[TPL], z[TPL], ev[TPL], rr[TPL];
-    unsigned vm[TPL];  // warp-uniform validity masks (bit = lane)
+// The cell's vertices live in shared memory slots; which slots are in use is kept in four warp-uniform
+// 32-bit masks (slot = 32 e + lane), with hw an upper bound of the used slots.
+template <int TP>
+struct CellState {
+    unsigned vm[TP];
+    int hw;
+    int np;
 };
 
-enum { R_OK = 0, R_NEED_EXACT = 1 };
+template <int TP>
+__device__ __forceinline__ void unpack(uint32_t id, uint32_t& a, uint32_t& b, uint32_t& c) {
+    typedef Cap<TP> K;
+    a = id & K::IDM; b = (id >> K::IDB) & K::IDM; c = (id >> (2 * K::IDB)) & K::IDM;
+}
+template <int TP>
+__device__ __forceinline__ uint32_t pack(uint32_t a, uint32_t b, uint32_t c) {
+    typedef Cap<TP> K;
+    return a | (b << K::IDB) | (c << (2 * K::IDB));
+}
+__device__ __forceinline__ uint32_t adj_get(uint32_t adj, int k) { return (adj >> (10 * k)) & 1023u; }
+__device__ __forceinline__ uint32_t adj_pack(uint32_t n0, uint32_t n1, uint32_t n2) {
+    return n0 | (n1 << 10) | (n2 << 20);
+}
+// position of plane p in a packed triangle (0, 1 or 2)
+template <int TP>
+__device__ __forceinline__ int pos_of(uint32_t id, uint32_t p) {
+    uint32_t a, b, c;
+    unpack<TP>(id, a, b, c);
+    return a == p ? 0 : (b == p ? 1 : 2);
+}
+// is slot n in the mask set m[]
+template <int TP>
+__device__ __forceinline__ bool in_mask(const unsigned* m, uint32_t n) {
+    bool r = false;
+#pragma unroll
+    for (int q = 0; q < TP; q++)
+        if ((int)(n >> 5) == q) r = ((m[q] >> (n & 31)) & 1u) != 0;
+    return r;
+}
 
 struct CellCounters {
-    unsigned n_cut, n_tested, n_passes, n_fp64, n_exact, n_zero;
+    unsigned n_cut, n_tested, n_passes, n_fp64, n_exact, n_zero, n_collect, n_collected;
+#ifdef VT_PHASE_TIMERS
+    unsigned long long t[10];  // cycles: collect, sort, test, cut, emit, total, apply_cut, retest, box, inf-bound tests
+#endif
 };
 
-template <typename CT>
-__device__ __forceinline__ void set_plane(WarpSmem<CT>& S, int p, CT nx, CT ny, CT nz, CT h, CT nrm, uint32_t src,
-                                          int code) {
-    if (lane_id() == 0) {
+// Optional per-phase cycle counters (compile with -DVT_PHASE_TIMERS; off in normal builds).
+#ifdef VT_PHASE_TIMERS
+#define VT_T0(name) long long name = clock64()
+#define VT_T1(cc, k, name) (cc).t[k] += (unsigned long long)(clock64() - name)
+#else
+#define VT_T0(name)
+#define VT_T1(cc, k, name)
+#endif
+
+// Capacity failures carry a reason (reported through the device status): -100 - reason.
+constexpr int CAP_PLANES = -101, CAP_TRIS = -102, CAP_BOUNDARY = -103, CAP_CAND = -104, CAP_STACK = -105,
+              CAP_FACETS = -106;
+
+template <typename CT, int TP>
+__device__ __forceinline__ void tri_vertex(WarpSmem<CT, TP>& S, int s) {
+    typedef Cap<TP> K;
+    uint32_t a, b, c;
+    unpack<TP>(S.tid[s], a, b, c);
+    make_vertex<CT>(S.pnx[a], S.pny[a], S.pnz[a], S.ph[a], S.pnrm[a], S.pnx[b], S.pny[b], S.pnz[b], S.ph[b], S.pnrm[b],
+                    S.pnx[c], S.pny[c], S.pnz[c], S.ph[c], S.pnrm[c], S.tx[s], S.ty[s], S.tz[s], S.tev[s], S.trr[s]);
+}
+
+// Drop the planes that no vertex uses any more (their facets were cut away) and renumber the rest; the six
+// initial planes keep ids 0..5.  Entries only move to lower ids, so each chunk of 32 is read, then written
+// in place.  Returns the new plane count.
+template <typename CT, int TP>
+__device__ __noinline__ int compact_planes(WarpSmem<CT, TP>& S, const unsigned* vm, int np) {
+    typedef Cap<TP> K;
+    const unsigned lane = lane_id(), lt = lanemask_lt();
+    for (int p = (int)lane; p < K::MAXP; p += 32) S.live[p] = (p < 6) ? 1 : 0;
+    __syncwarp();
+    for (int e = 0; e < TP; e++)
+        if ((vm[e] >> lane) & 1u) {
+            uint32_t a, b, c;
+            unpack<TP>(S.tid[e * 32 + lane], a, b, c);
+            S.live[a] = 1; S.live[b] = 1; S.live[c] = 1;
+        }
+    __syncwarp();
+    int base = 0;
+    for (int c = 0; c < K::MAXP / 32; c++) {
+        int p = c * 32 + (int)lane;
+        bool lv = p < np && S.live[p];
+        CT qx = 0, qy = 0, qz = 0, qh = 0, qn = 0;
+        uint32_t qs = 0;
+        uint8_t qc = 0;
+        if (lv) {
+            qx = S.pnx[p]; qy = S.pny[p]; qz = S.pnz[p]; qh = S.ph[p]; qn = S.pnrm[p];
+            qs = S.psrc[p]; qc = S.pcode[p];
+        }
+        unsigned m = __ballot_sync(0xffffffffu, lv);
+        int q = base + __popc(m & lt);
+        base += __popc(m);
+        __syncwarp();
+        if (lv) {
+            S.pnx[q] = qx; S.pny[q] = qy; S.pnz[q] = qz; S.ph[q] = qh; S.pnrm[q] = qn;
+            S.psrc[q] = qs; S.pcode[q] = qc;
+            S.live[p] = (uint16_t)q;  // now the renumbering table
+        }
+        __syncwarp();
+    }
+    for (int e = 0; e < TP; e++)
+        if ((vm[e] >> lane) & 1u) {
+            int t = e * 32 + lane;
+            uint32_t a, b, c;
+            unpack<TP>(S.tid[t], a, b, c);
+            S.tid[t] = pack<TP>(S.live[a], S.live[b], S.live[c]);
+        }
+    __syncwarp();
+    return base;
+}
+
+// Side of vertex slot s w.r.t. the lane's plane in the working precision: +1 strictly beyond, -1 strictly
+// inside, 0 when the error bound does not decide.
+template <typename CT, int TP>
+__device__ __forceinline__ int side_fast(const WarpSmem<CT, TP>& S, int s, CT nx, CT ny, CT nz, CT h, CT nrm, CT hb) {
+    CT sv = f_fma<CT>(nx, S.tx[s], f_fma<CT>(ny, S.ty[s], f_fma<CT>(nz, S.tz[s], -h)));
+    CT bound = f_fma<CT>(nrm, S.tev[s], hb);
+    if (sv > bound) return 1;
+    if (sv < -bound) return -1;
+    return 0;  // includes NaN / infinite bounds
+}
+
+// Decide the lanes flagged `need` (vertex slot s against each lane's plane): FP64 from the inputs in the FP32
+// kernels, then exact expansion arithmetic in the exact kernel (lanes take the warp's workspace in turn).
+// Returns +1/-1 per lane (0 if undecided in a non-exact kernel: *need_exact is set).
+template <typename P, typename CT, bool EXACT, int TP>
+__device__ int resolve(const WarpSmem<CT, TP>& S, int s, bool need, uint32_t src, int code, const P* spos,
+                       const Geometry& g, uint32_t self, double* xws, CellCounters& cc, bool& need_exact,
+                       bool& ovf) {
+    const unsigned lane = lane_id();
+    int sd = 0;
+    uint32_t a, b, c;
+    unpack<TP>(S.tid[s], a, b, c);
+    PRef ra = {S.psrc[a], S.pcode[a]}, rb = {S.psrc[b], S.pcode[b]}, rc = {S.psrc[c], S.pcode[c]};
+    PRef rj = {src, code};
+    if (need && sizeof(CT) == 4) {
+        sd = side64<P>(spos, g, self, ra, rb, rc, rj);
+        cc.n_fp64++;
+#ifdef VT_PHASE_TIMERS
+        if (!(S.tev[s] < (CT)INFINITY)) cc.t[9]++;
+#endif
+    }
+    bool pending = need && sd == 0;
+    if (!EXACT) {
+        if (pending) need_exact = true;
+        return sd;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, pending);
+    while (todo) {
+        int L = __ffs(todo) - 1;
+        if ((int)lane == L) {
+            bool o = false;
+            sd = exact_side<P>(xws, spos, g, self, ra, rb, rc, rj, &o);
+            cc.n_exact++;
+            if (o) ovf = true;
+            if (sd == 0) cc.n_zero++;
+            if (sd == 0) sd = -1;  // on the plane: kept (not strictly beyond)
+        }
+        __syncwarp();
+        todo &= todo - 1;
+    }
+    return sd;
+}
+
+// Cut the cell by a plane known to remove exactly the vertex slots rem[].  The plane gets an id; every edge
+// x->y of a removed triangle whose neighbour across it is kept lies on the boundary of the removed region and
+// becomes a new triangle (x, y, p) in the lowest free slot.  Adjacency: across x->y the kept neighbour (whose
+// pointer is redirected to the new triangle), across y->p the new triangle starting at y, across p->x the
+// new triangle ending at x.  newm[] returns the new slots.  Returns 0 or a CAP_* code.
+template <typename CT, int TP>
+__device__ int apply_cut(WarpSmem<CT, TP>& S, CellState<TP>& C, const unsigned* rem, CT nx, CT ny, CT nz, CT h, CT nrm,
+                         uint32_t src, int code, unsigned* newm) {
+    typedef Cap<TP> K;
+    const unsigned lane = lane_id(), lt = lanemask_lt();
+    if (C.np >= K::MAXP) {
+        C.np = compact_planes<CT, TP>(S, C.vm, C.np);
+        if (C.np >= K::MAXP) return CAP_PLANES;
+    }
+    const int p = C.np++;
+    if (lane == 0) {
         S.pnx[p] = nx; S.pny[p] = ny; S.pnz[p] = nz; S.ph[p] = h; S.pnrm[p] = nrm;
         S.psrc[p] = src; S.pcode[p] = (uint8_t)code;
     }
-}
-
-template <typename CT>
-__device__ __forceinline__ void vertex_from_planes(const WarpSmem<CT>& S, int a, int b, int c, CT& vx, CT& vy, CT& vz,
-                                                   CT& ev, CT& rr) {
-    make_vertex<CT>(S.pnx[a], S.pny[a], S.pnz[a], S.ph[a], S.pnrm[a], S.pnx[b], S.pny[b], S.pnz[b], S.ph[b], S.pnrm[b],
-                    S.pnx[c], S.pny[c], S.pnz[c], S.ph[c], S.pnrm[c], vx, vy, vz, ev, rr);
-}
-
-// Clip by a candidate plane.  Returns 0 (no cut), 1 (cut), R_NEED_EXACT encoded as 2, or a VT_ERR_* (<0).
-template <typename P, typename CT, bool EXACT>
-__device__ int clip_plane(WarpSmem<CT>& S, Tris<CT>& T, int& np, CT nx, CT ny, CT nz, CT h, CT nrm, uint32_t src,
-                          int code, const P* spos, const Geometry& g, uint32_t self, double* xws, CellCounters& cc) {
-    const unsigned lane = lane_id();
-    const CT u = Prec<CT>::u();
-    const CT hb = (CT)16 * u * h;
-    bool out[TPL];
-    bool unc_any = false;
-#pragma unroll
-    for (int e = 0; e < TPL; e++) {
-        out[e] = false;
-        if ((T.vm[e] >> lane) & 1u) {
-            CT s = f_fma<CT>(nx, T.x[e], f_fma<CT>(ny, T.y[e], f_fma<CT>(nz, T.z[e], -h)));
-            CT bound = f_fma<CT>(nrm, T.ev[e], hb);
-            if (s > bound) out[e] = true;
-            else if (!(s < -bound)) unc_any = true;  // also catches NaN / inf bounds
-        }
-    }
-    if (__any_sync(0xffffffffu, unc_any)) {
-        // undecided tests: FP64 from the input coordinates (FP32 kernels), then exactly (exact kernel)
-        bool need_exact = false;
-        bool pend[TPL];
-#pragma unroll
-        for (int e = 0; e < TPL; e++) {
-            pend[e] = false;
-            if ((T.vm[e] >> lane) & 1u) {
-                CT s = f_fma<CT>(nx, T.x[e], f_fma<CT>(ny, T.y[e], f_fma<CT>(nz, T.z[e], -h)));
-                CT bound = f_fma<CT>(nrm, T.ev[e], hb);
-                if (!(s > bound) && !(s < -bound)) {
-                    int sd = 0;
-                    if (sizeof(CT) == 4) {
-                        uint32_t id = T.id[e];
-                        int a = id & 255, b = (id >> 8) & 255, c = (id >> 16) & 255;
-                        PRef ra = {S.psrc[a], S.pcode[a]}, rb = {S.psrc[b], S.pcode[b]}, rc = {S.psrc[c], S.pcode[c]};
-                        PRef rj = {src, code};
-                        sd = side64<P>(spos, g, self, ra, rb, rc, rj);
-                        cc.n_fp64++;
-                    }
-                    if (sd != 0) out[e] = (sd > 0);
-                    else if (EXACT) pend[e] = true;
-                    else need_exact = true;
-                }
-            }
-        }
-        if (!EXACT) {
-            if (__any_sync(0xffffffffu, need_exact)) return 2;
-        } else {
-            bool mine = false;
-#pragma unroll
-            for (int e = 0; e < TPL; e++) mine |= pend[e];
-            unsigned todo = __ballot_sync(0xffffffffu, mine);
-            bool ovf_any = false;
-            while (todo) {
-                int L = __ffs(todo) - 1;
-                if ((int)lane == L) {  // one lane at a time owns the warp's workspace
-#pragma unroll
-                    for (int e = 0; e < TPL; e++) {
-                        if (pend[e]) {
-                            uint32_t id = T.id[e];
-                            int a = id & 255, b = (id >> 8) & 255, c = (id >> 16) & 255;
-                            PRef ra = {S.psrc[a], S.pcode[a]}, rb = {S.psrc[b], S.pcode[b]},
-                                 rc = {S.psrc[c], S.pcode[c]};
-                            PRef rj = {src, code};
-                            bool ovf = false;
-                            int sd = exact_side<P>(xws, spos, g, self, ra, rb, rc, rj, &ovf);
-                            cc.n_exact++;
-                            if (ovf) ovf_any = true;
-                            if (sd == 0) cc.n_zero++;
-                            out[e] = (sd > 0);
-                        }
-                    }
-                }
-                __syncwarp();
-                todo &= todo - 1;
-            }
-            if (__any_sync(0xffffffffu, ovf_any)) return VT_ERR_NUMERIC;
-        }
-    }
-    // which slots are removed
-    unsigned om[TPL];
-    bool any = false;
-#pragma unroll
-    for (int e = 0; e < TPL; e++) {
-        om[e] = __ballot_sync(0xffffffffu, out[e]);
-        any |= (om[e] != 0);
-    }
-    if (!any) return 0;
-    if (np >= MAXP) return VT_ERR_CAPACITY;
-    const int p = np++;
-    set_plane<CT>(S, p, nx, ny, nz, h, nrm, src, code);
-    // directed edges of the removed triangles
-    int nE = 0;
-    const unsigned lt = lanemask_lt();
-#pragma unroll
-    for (int e = 0; e < TPL; e++) {
-        if (om[e]) {
-            if (out[e]) {
-                int o = nE + 3 * __popc(om[e] & lt);
-                uint32_t id = T.id[e];
-                uint32_t a = id & 255, b = (id >> 8) & 255, c = (id >> 16) & 255;
-                S.edges[o + 0] = (uint16_t)((a << 8) | b);
-                S.edges[o + 1] = (uint16_t)((b << 8) | c);
-                S.edges[o + 2] = (uint16_t)((c << 8) | a);
-            }
-            nE += 3 * __popc(om[e]);
-            T.vm[e] &= ~om[e];
-        }
-    }
-    __syncwarp();
-    // boundary edges: directed edges whose reverse is not among them
+    // boundary records
     int nB = 0;
-    for (int k0 = 0; k0 < nE; k0 += 32) {
-        int k = k0 + (int)lane;
-        bool bnd = false;
-        uint16_t ed = 0;
-        if (k < nE) {
-            ed = S.edges[k];
-            uint16_t rev = (uint16_t)((ed >> 8) | ((ed & 255) << 8));
-            bnd = true;
-            for (int q = 0; q < nE; q++)
-                if (S.edges[q] == rev) { bnd = false; break; }
+#pragma unroll
+    for (int e = 0; e < TP; e++) {
+        if (!rem[e]) continue;
+        const bool mine = (rem[e] >> lane) & 1u;
+        uint32_t ids[3] = {0u, 0u, 0u}, adj = 0u;
+        const uint32_t t = e * 32 + lane;
+        if (mine) {
+            unpack<TP>(S.tid[t], ids[0], ids[1], ids[2]);
+            adj = S.tadj[t];
         }
-        unsigned bm = __ballot_sync(0xffffffffu, bnd);
-        if (bnd) {
-            int o = nB + __popc(bm & lt);
-            if (o < MAXT) S.bnd[o] = ed;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            uint32_t n = adj_get(adj, k);
+            bool bnd = mine && !in_mask<TP>(rem, n);
+            unsigned bm = __ballot_sync(0xffffffffu, bnd);
+            if (bnd) {
+                int o = nB + __popc(bm & lt);
+                uint32_t nadj = S.tadj[n];
+                uint32_t kn = adj_get(nadj, 0) == t ? 0u : (adj_get(nadj, 1) == t ? 1u : 2u);
+                if (o < K::MAXT)
+                    S.bnd[o] = ids[k] | (ids[(k + 1) % 3] << K::IDB) | (n << (2 * K::IDB)) | (kn << (2 * K::IDB + K::SB));
+            }
+            nB += __popc(bm);
         }
-        nB += __popc(bm);
+        C.vm[e] &= ~rem[e];
     }
     __syncwarp();
-    if (nB > MAXT) return VT_ERR_CAPACITY;
-    // new triangles (x, y, p) into the lowest free slots
+    if (nB > K::MAXT) return CAP_BOUNDARY;
+    // new triangles into the lowest free slots; link tables by plane id
     int placed = 0;
+    int myrank[TP];
 #pragma unroll
-    for (int e = 0; e < TPL; e++) {
-        unsigned fm = ~T.vm[e];
+    for (int e = 0; e < TP; e++) {
+        unsigned fm = ~C.vm[e];
         int rank = placed + __popc(fm & lt);
-        bool mine = ((fm >> lane) & 1u) && rank < nB;
-        if (mine) {
-            uint16_t ed = S.bnd[rank];
-            int x = ed >> 8, y = ed & 255;
-            T.id[e] = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)p << 16);
-            vertex_from_planes<CT>(S, x, y, p, T.x[e], T.y[e], T.z[e], T.ev[e], T.rr[e]);
+        bool mk = ((fm >> lane) & 1u) && rank < nB;
+        myrank[e] = mk ? rank : -1;
+        if (mk) {
+            uint32_t r = S.bnd[rank];
+            uint32_t x = r & K::IDM, y = (r >> K::IDB) & K::IDM;
+            S.lnk_s[x] = (uint16_t)(e * 32 + lane);
+            S.lnk_e[y] = (uint16_t)(e * 32 + lane);
         }
-        unsigned nm = __ballot_sync(0xffffffffu, mine);
-        T.vm[e] |= nm;
+        unsigned nm = __ballot_sync(0xffffffffu, mk);
+        newm[e] = nm;
+        C.vm[e] |= nm;
+        if (nm) C.hw = max(C.hw, e * 32 + 32 - __clz(nm));
         placed += __popc(fm);
     }
-    if (placed < nB) return VT_ERR_CAPACITY;
-    cc.n_cut++;
-    return 1;
+    if (placed < nB) return CAP_TRIS;
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < TP; e++) {
+        if (myrank[e] >= 0) {
+            const uint32_t t = e * 32 + lane;
+            uint32_t r = S.bnd[myrank[e]];
+            uint32_t x = r & K::IDM, y = (r >> K::IDB) & K::IDM;
+            uint32_t n = (r >> (2 * K::IDB)) & ((1u << K::SB) - 1u), kn = r >> (2 * K::IDB + K::SB);
+            S.tid[t] = pack<TP>(x, y, (uint32_t)p);
+            S.tadj[t] = adj_pack(n, S.lnk_s[y], S.lnk_e[x]);
+            // redirect the kept neighbour's pointer (fields of one word may be updated by two new triangles)
+            atomicAnd(&S.tadj[n], ~(1023u << (10 * kn)));
+            atomicOr(&S.tadj[n], t << (10 * kn));
+            tri_vertex<CT, TP>(S, t);
+        }
+    }
+    __syncwarp();
+    return 0;
 }
 
-template <typename CT>
-__device__ __forceinline__ CT rmax2(const Tris<CT>& T) {
+template <typename CT, int TP>
+__device__ __forceinline__ CT rmax2(const WarpSmem<CT, TP>& S, const CellState<TP>& C) {
     CT r = 0;
     const unsigned lane = lane_id();
 #pragma unroll
-    for (int e = 0; e < TPL; e++)
-        if ((T.vm[e] >> lane) & 1u) r = r > T.rr[e] ? r : T.rr[e];
+    for (int e = 0; e < TP; e++)
+        if ((C.vm[e] >> lane) & 1u) {
+            CT v = S.trr[e * 32 + lane];
+            r = r > v ? r : v;
+        }
     return warp_max<CT>(r);
 }
 
+// Box around the exact vertices (positions widened by their error bounds), as floats rounded outward.
+template <typename CT, int TP>
+__device__ __forceinline__ void cell_box(const WarpSmem<CT, TP>& S, const CellState<TP>& C, float* bmin, float* bmax) {
+    const unsigned lane = lane_id();
+    float lo0 = 0.f, lo1 = 0.f, lo2 = 0.f, hi0 = 0.f, hi1 = 0.f, hi2 = 0.f;  // the site is inside
+    bool inf = false;
+#pragma unroll
+    for (int e = 0; e < TP; e++)
+        if ((C.vm[e] >> lane) & 1u) {
+            int s = e * 32 + lane;
+            CT ev = S.tev[s];
+            if (!(ev < (CT)INFINITY)) inf = true;
+            lo0 = fminf(lo0, __double2float_rd((double)(S.tx[s] - ev)));
+            lo1 = fminf(lo1, __double2float_rd((double)(S.ty[s] - ev)));
+            lo2 = fminf(lo2, __double2float_rd((double)(S.tz[s] - ev)));
+            hi0 = fmaxf(hi0, __double2float_ru((double)(S.tx[s] + ev)));
+            hi1 = fmaxf(hi1, __double2float_ru((double)(S.ty[s] + ev)));
+            hi2 = fmaxf(hi2, __double2float_ru((double)(S.tz[s] + ev)));
+        }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+        lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+        lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+        hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+        hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+        hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+    }
+    if (__any_sync(0xffffffffu, inf)) {  // unknown vertex: no filtering
+        lo0 = lo1 = lo2 = -INFINITY;
+        hi0 = hi1 = hi2 = INFINITY;
+    }
+    bmin[0] = lo0; bmin[1] = lo1; bmin[2] = lo2;
+    bmax[0] = hi0; bmax[1] = hi1; bmax[2] = hi2;
+}
+
 // ------------------------------------------------------------------ tree search
+// Support-function filter.  With [bmin, bmax] (bmin <= 0 <= bmax) a box around the exact vertices of the cell
+// (site at the origin), a point p can cut the cell only if some vertex v has 2 p.v > |p|^2, and
+// p.v <= sum_a max(p_a bmin_a, p_a bmax_a); so p cannot cut when
+//     sum_a g_a(p_a) <= 0,   g_a(t) = 2 max(t bmin_a, t bmax_a) - t^2.
+// g_a is concave on each sign of t, with its peak at bmax_a (t >= 0) and at bmin_a (t <= 0).
+__device__ __forceinline__ float supp_g(float t, float bmin, float bmax) {
+    return 2.f * fmaxf(t * bmin, t * bmax) - t * t;
+}
+// largest g over [t0, t1]
+__device__ __forceinline__ float supp_gmax(float t0, float t1, float bmin, float bmax) {
+    float best = -INFINITY;
+    if (t1 >= 0.f) best = fmaxf(best, supp_g(fminf(fmaxf(bmax, fmaxf(t0, 0.f)), t1), bmin, bmax));
+    if (t0 <= 0.f) best = fmaxf(best, supp_g(fmaxf(fminf(bmin, fminf(t1, 0.f)), t0), bmin, bmax));
+    return best;
+}
+// largest g over the node's extent along one axis, relative to q, for its minimum-image shifts
+__device__ __forceinline__ float supp_axis(float q, float lo, float hi, float L, int periodic, float bmin,
+                                           float bmax) {
+    float m = supp_gmax(lo - q, hi - q, bmin, bmax);
+    if (periodic) {
+        m = fmaxf(m, supp_gmax(lo - q - L, hi - q - L, bmin, bmax));
+        m = fmaxf(m, supp_gmax(lo - q + L, hi - q + L, bmin, bmax));
+    }
+    return m;
+}
+
+// upper bound of the (minimum-image) distance along one axis from q to any point of [lo, hi]
+__device__ __forceinline__ float axis_far(float q, float lo, float hi, float L, int periodic) {
+    float d = fmaxf(fabsf(q - lo), fabsf(q - hi));
+    if (periodic) {
+        d = fminf(d, fmaxf(fabsf(q - lo - L), fabsf(q - hi - L)));
+        d = fminf(d, fmaxf(fabsf(q - lo + L), fabsf(q - hi + L)));
+    }
+    return d;
+}
 __device__ __forceinline__ float axis_gap(float q, float lo, float hi, float L, int periodic) {
     float d = fmaxf(fmaxf(lo - q, q - hi), 0.f);
     if (periodic) {
@@ -614,14 +806,26 @@ __device__ __forceinline__ float axis_gap(float q, float lo, float hi, float L, 
 }
 
 // Collect sorted indices j != self with rlo2 <= |d|^2 < rhi2 (the same |d|^2 as the clipping loop).
-// Returns the count, or -1 if more than CAND_CAP, or -2 on stack overflow.
-template <typename P, typename CT>
-__device__ int collect(WarpSmem<CT>& S, const P* spos, int64_t N, const Geometry& g, const Tree& t, uint32_t self,
-                       const P& pi, CT rlo2, CT rhi2) {
+// Every hit is also counted in a radial histogram of |d|^2 over [rlo2, rhi2) (HIST_BINS bins), so that an
+// overflowing pass can pick a smaller rhi2 that fits.  Returns the count (which may exceed the capacity: only the
+// first Cap::CAND are stored) or -2 on stack overflow.
+template <typename P, typename CT, int TP>
+__device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geometry& g, const Tree& t, uint32_t self,
+                       const P& pi, CT rlo2, CT rhi2, const float* bmin, const float* bmax) {
     const unsigned lane = lane_id(), lt = lanemask_lt();
+    for (int k = (int)lane; k < HIST_BINS; k += 32) S.hist[k] = 0u;
+    __syncwarp();
+    // bins over the bit patterns of the non-negative |d|^2 (monotone), so narrowing never underflows
+    const unsigned long long blo = fbits<CT>(rlo2), bhi = fbits<CT>(rhi2);
+    const unsigned long long bwidth = bhi > blo ? bhi - blo : 1ull;
     // conservative float radius for box pruning
     float rad = (float)sqrt((double)rhi2) * 1.0001f + 1e-30f;
     float rad2 = rad * rad;
+    // nodes entirely within the inner radius hold only examined points
+    float inner2 = (float)((double)rlo2 * 0.9999);
+    // rounding tolerance of the support test: relative 1e-5 of its terms
+    const float bext = fmaxf(fmaxf(fmaxf(-bmin[0], bmax[0]), fmaxf(-bmin[1], bmax[1])), fmaxf(-bmin[2], bmax[2]));
+    const float stol = 1e-5f * (4.f * bext * rad + rad2) + 1e-30f;
     float qx = (float)pi.x, qy = (float)pi.y, qz = (float)pi.z;
     // float rounding of q: widen by one ulp of the box scale
     float slack = 2.0f * 1.2e-7f * fmaxf(fmaxf(fabsf(g.hif[0]), fabsf(g.lof[0])),
@@ -638,6 +842,12 @@ __device__ int collect(WarpSmem<CT>& S, const P* spos, int64_t N, const Geometry
             float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], g.periodic) - slack, 0.f);
             float dz = fmaxf(axis_gap(qz, lo.z, hi.z, g.Lf[2], g.periodic) - slack, 0.f);
             hit = dx * dx + dy * dy + dz * dz <= rad2;
+            if (hit) {
+                float sx = supp_axis(qx, lo.x - slack, hi.x + slack, g.Lf[0], g.periodic, bmin[0], bmax[0]);
+                float sy = supp_axis(qy, lo.y - slack, hi.y + slack, g.Lf[1], g.periodic, bmin[1], bmax[1]);
+                float sz = supp_axis(qz, lo.z - slack, hi.z + slack, g.Lf[2], g.periodic, bmin[2], bmax[2]);
+                if (sx + sy + sz < -stol) hit = false;
+            }
         }
         unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) S.stack[__popc(m & lt)] = ((uint32_t)top << 27) | lane;
@@ -655,23 +865,38 @@ __device__ int collect(WarpSmem<CT>& S, const P* spos, int64_t N, const Geometry
             int64_t j = node * 32 + lane;
             bool hit = false;
             unsigned long long key = 0ull;
+            CT d2 = (CT)0, dx = (CT)0, dy = (CT)0, dz = (CT)0;
+            int code = 13;
             if (j < N && (uint32_t)j != self) {
                 P pj = spos[j];
-                CT dx, dy, dz;
-                int code;
                 DispF<P, CT>::get(pj, pi, g, dx, dy, dz, code);
-                CT d2 = f_fma<CT>(dz, dz, f_fma<CT>(dy, dy, dx * dx));
+                d2 = f_fma<CT>(dz, dz, f_fma<CT>(dy, dy, dx * dx));
                 hit = (d2 >= rlo2) && (d2 < rhi2);
+                if (hit) {
+                    float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+                    float sg = supp_g(fx, bmin[0], bmax[0]) + supp_g(fy, bmin[1], bmax[1]) + supp_g(fz, bmin[2], bmax[2]);
+                    if (sg < -stol) hit = false;
+                }
                 // order-preserving key: d2 >= 0 so its float bits sort like the value; FP64 values are
                 // rounded down so that a key never exceeds the |d|^2 it stands for
                 float kf = (sizeof(CT) == 4) ? (float)d2 : __double2float_rd((double)d2);
-                key = ((unsigned long long)__float_as_uint(kf) << 32) | (uint32_t)j;
+                key = (unsigned long long)__float_as_uint(kf) << 32;
             }
             unsigned m = __ballot_sync(0xffffffffu, hit);
             int o = count + __popc(m & lt);
-            if (hit && o < CAND_CAP) S.u.cand[o] = key;
+            if (hit && o < Cap<TP>::CAND) {
+                S.u.cd.key[o] = key | (uint32_t)o;
+                S.u.cd.dx[o] = dx; S.u.cd.dy[o] = dy; S.u.cd.dz[o] = dz;
+                S.u.cd.j[o] = (uint32_t)j;
+                S.u.cd.code[o] = (uint8_t)code;
+            }
+            if (hit) {
+                unsigned long long bb = fbits<CT>(d2);
+                int b = bb <= blo ? 0 : (int)min((unsigned long long)(HIST_BINS - 1),
+                                                 (unsigned long long)((double)(bb - blo) * HIST_BINS / (double)bwidth));
+                atomicAdd(&S.hist[b], 1u);
+            }
             count += __popc(m);
-            if (count > CAND_CAP) return -1;
         } else {
             int cl = lvl - 1;
             int64_t c = node * 32 + lane;
@@ -682,9 +907,23 @@ __device__ int collect(WarpSmem<CT>& S, const P* spos, int64_t N, const Geometry
                 float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], g.periodic) - slack, 0.f);
                 float dz = fmaxf(axis_gap(qz, lo.z, hi.z, g.Lf[2], g.periodic) - slack, 0.f);
                 hit = dx * dx + dy * dy + dz * dz <= rad2;
+                if (hit && inner2 > 0.f) {
+                    // every point of the node already examined in an earlier pass: skip it
+                    float fx = axis_far(qx, lo.x, hi.x, g.Lf[0], g.periodic) + slack;
+                    float fy = axis_far(qy, lo.y, hi.y, g.Lf[1], g.periodic) + slack;
+                    float fz = axis_far(qz, lo.z, hi.z, g.Lf[2], g.periodic) + slack;
+                    if (fx * fx + fy * fy + fz * fz < inner2) hit = false;
+                }
+                if (hit) {
+                    // no point of the node can cut the cell (node widened by the rounding slack of q)
+                    float sx = supp_axis(qx, lo.x - slack, hi.x + slack, g.Lf[0], g.periodic, bmin[0], bmax[0]);
+                    float sy = supp_axis(qy, lo.y - slack, hi.y + slack, g.Lf[1], g.periodic, bmin[1], bmax[1]);
+                    float sz = supp_axis(qz, lo.z - slack, hi.z + slack, g.Lf[2], g.periodic, bmin[2], bmax[2]);
+                    if (sx + sy + sz < -stol) hit = false;
+                }
             }
             unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (sp + __popc(m) > STACK_CAP) return -2;
+            if (sp + __popc(m) > Cap<TP>::STACK) return -2;
             if (hit) S.stack[sp + __popc(m & lt)] = ((uint32_t)cl << 27) | (uint32_t)c;
             sp += __popc(m);
             __syncwarp();
@@ -693,23 +932,24 @@ __device__ int collect(WarpSmem<CT>& S, const P* spos, int64_t N, const Geometry
     return count;
 }
 
-// bitonic sort of S.u.cand[0..n) (padded to a power of two with +inf keys)
-template <typename CT>
-__device__ void sort_cand(WarpSmem<CT>& S, int n) {
+// bitonic sort of the candidate keys [0..n) (padded to a power of two with +inf keys); equal distances
+// fall back to the collection slot, which is deterministic for a given input
+template <typename CT, int TP>
+__device__ void sort_cand(WarpSmem<CT, TP>& S, int n) {
     const unsigned lane = lane_id();
     int m = 1;
     while (m < n) m <<= 1;
     if (m < 2) return;
-    for (int k = n + (int)lane; k < m; k += 32) S.u.cand[k] = ~0ull;
+    for (int k = n + (int)lane; k < m; k += 32) S.u.cd.key[k] = ~0ull;
     __syncwarp();
     for (int k = 2; k <= m; k <<= 1) {
         for (int jj = k >> 1; jj > 0; jj >>= 1) {
             for (int i = (int)lane; i < m; i += 32) {
                 int ixj = i ^ jj;
                 if (ixj > i) {
-                    unsigned long long a = S.u.cand[i], b = S.u.cand[ixj];
+                    unsigned long long a = S.u.cd.key[i], b = S.u.cd.key[ixj];
                     bool asc = (i & k) == 0;
-                    if ((a > b) == asc) { S.u.cand[i] = b; S.u.cand[ixj] = a; }
+                    if ((a > b) == asc) { S.u.cd.key[i] = b; S.u.cd.key[ixj] = a; }
                 }
             }
             __syncwarp();
@@ -721,34 +961,49 @@ __device__ void sort_cand(WarpSmem<CT>& S, int n) {
 constexpr int RC_NEED_EXACT = 1000;
 constexpr int RC_POOL = 1001;
 
-// successor of triangle t around plane p: the triangle holding the directed edge p -> (corner before p in t)
-template <typename CT>
-__device__ __forceinline__ uint32_t succ_tri(const WarpSmem<CT>& S, uint32_t t, int p) {
-    uint32_t id = S.u.em.tid[t];
-    uint32_t a = id & 255, b = (id >> 8) & 255, c = (id >> 16) & 255;
-    uint32_t before = (a == (uint32_t)p) ? c : (b == (uint32_t)p) ? a : b;
-    uint32_t key = ((uint32_t)p << 8) | before;
-    uint32_t hsh = (key * 2654435761u) >> 23;
-    for (int probe = 0; probe < HASH_SZ; probe++) {
-        uint32_t ent = S.u.em.hash[hsh];
-        if (ent == 0xffffffffu) return 0xffffffffu;
-        if ((ent >> 8) == key) return ent & 255;
-        hsh = (hsh + 1) & (HASH_SZ - 1);
-    }
-    return 0xffffffffu;
+// successor of triangle t around plane p: the neighbour across the edge (corner before p) -> p
+template <typename CT, int TP>
+__device__ __forceinline__ uint32_t succ_tri(const WarpSmem<CT, TP>& S, uint32_t t, int p) {
+    int k = pos_of<TP>(S.tid[t], (uint32_t)p);
+    return adj_get(S.tadj[t], (k + 2) % 3);
 }
 
-template <typename P, typename CT, bool EXACT>
-__device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double* xws, CellCounters& cc) {
+// Test the lanes' planes against the vertex slots in masks[] and OR the beyond-the-plane slots into outm[].
+template <typename P, typename CT, bool EXACT, int TP>
+__device__ __forceinline__ void test_slots(const WarpSmem<CT, TP>& S, const unsigned* masks, bool act, CT nx, CT ny, CT nz,
+                                           CT h, CT nrm, CT hb, uint32_t src, int code, unsigned* outm,
+                                           const P* spos, const Geometry& g, uint32_t self, double* xws,
+                                           CellCounters& cc, bool& need_exact, bool& ovf) {
+#pragma unroll
+    for (int e = 0; e < TP; e++) {
+        unsigned m = masks[e];
+        while (m) {
+            int l = __ffs(m) - 1;
+            m &= m - 1;
+            int s = e * 32 + l;
+            int sd = act ? side_fast<CT, TP>(S, s, nx, ny, nz, h, nrm, hb) : -1;
+            bool und = act && sd == 0;
+            if (__any_sync(0xffffffffu, und)) {  // every lane calls: resolve may use warp collectives
+                int r = resolve<P, CT, EXACT, TP>(S, s, und, src, code, spos, g, self, xws, cc, need_exact, ovf);
+                if (und) sd = r;
+            }
+            if (sd > 0) outm[e] |= 1u << l;
+        }
+    }
+}
+
+template <typename P, typename CT, bool EXACT, int TP>
+__device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, double* xws, CellCounters& cc) {
     const P* spos = (const P*)A.spos;
     const Geometry& g = A.geo;
     const unsigned lane = lane_id(), lt = lanemask_lt();
     const CT u = Prec<CT>::u();
     const P pi = spos[self];
-    Tris<CT> T;
+    typedef Cap<TP> K;
+    CellState<TP> C;
 #pragma unroll
-    for (int e = 0; e < TPL; e++) T.vm[e] = 0u;
-    int np = 6;
+    for (int e = 0; e < TP; e++) C.vm[e] = 0u;
+    C.np = 6;
     // initial planes: periodic self-images (+x,-x,+y,-y,+z,-z) or box walls
     if (lane < 6) {
         int axis = lane >> 1;
@@ -761,9 +1016,9 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
             if (axis == 0) nx = sg; else if (axis == 1) ny = sg; else nz = sg;
             h = (CT)(0.5 * g.L[axis] * g.L[axis]);
             nrm = Lc;
-            int s[3] = {0, 0, 0};
-            s[axis] = upper ? 1 : -1;
-            code = (s[0] + 1) + 3 * (s[1] + 1) + 9 * (s[2] + 1);
+            int sh[3] = {0, 0, 0};
+            sh[axis] = upper ? 1 : -1;
+            code = code_of(sh[0], sh[1], sh[2]);
         } else {
             CT sg = upper ? (CT)1 : (CT)-1;
             if (axis == 0) nx = sg; else if (axis == 1) ny = sg; else nz = sg;
@@ -776,20 +1031,38 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
         S.psrc[lane] = self; S.pcode[lane] = (uint8_t)code;
     }
     __syncwarp();
-    // 8 corners: plane ids upper x=0/lower x=1, y 2/3, z 4/5; orientation (X,Y,Z) if the sign product is
-    // positive, else (X,Z,Y): every triangle then lists its planes counter-clockwise seen from outside
+    // 8 corners: planes x upper 0 / lower 1, y 2/3, z 4/5; (X,Y,Z) if the sign product is positive, else
+    // (X,Z,Y): every triangle then lists its planes counter-clockwise seen from outside
     if (lane < 8) {
         int sx = (lane & 1) ? -1 : 1, sy = (lane & 2) ? -1 : 1, sz = (lane & 4) ? -1 : 1;
         uint32_t X = (lane & 1) ? 1 : 0, Y = (lane & 2) ? 3 : 2, Z = (lane & 4) ? 5 : 4;
-        uint32_t id = (sx * sy * sz > 0) ? (X | (Y << 8) | (Z << 16)) : (X | (Z << 8) | (Y << 16));
-        T.id[0] = id;
-        vertex_from_planes<CT>(S, id & 255, (id >> 8) & 255, (id >> 16) & 255, T.x[0], T.y[0], T.z[0], T.ev[0],
-                               T.rr[0]);
+        S.tid[lane] = (sx * sy * sz > 0) ? pack<TP>(X, Y, Z) : pack<TP>(X, Z, Y);
+        tri_vertex<CT, TP>(S, lane);
     }
-    T.vm[0] = 0xFFu;
-    CT R2 = rmax2<CT>(T);
+    __syncwarp();
+    if (lane < 8) {  // adjacency of the initial octahedron by search
+        uint32_t ids[3];
+        unpack<TP>(S.tid[lane], ids[0], ids[1], ids[2]);
+        uint32_t nb[3] = {0u, 0u, 0u};
+        for (int k = 0; k < 3; k++) {
+            uint32_t x = ids[k], y = ids[(k + 1) % 3];
+            for (int t2 = 0; t2 < 8; t2++) {
+                uint32_t o[3];
+                unpack<TP>(S.tid[t2], o[0], o[1], o[2]);
+                for (int q = 0; q < 3; q++)
+                    if (o[q] == y && o[(q + 1) % 3] == x) nb[k] = (uint32_t)t2;
+            }
+        }
+        S.tadj[lane] = adj_pack(nb[0], nb[1], nb[2]);
+    }
+    C.vm[0] = 0xFFu;
+    C.hw = 8;
+    __syncwarp();
+    CT R2 = rmax2<CT, TP>(S, C);
+    float bmin[3], bmax[3];
+    cell_box<CT, TP>(S, C, bmin, bmax);
 
-    // first radius from the bucket mates: 1.6 x the distance of the ~12th nearest
+    // first radius from the bucket mates: 1.6 x the distance of the ~11th nearest
     CT rhi2;
     {
         int64_t b0 = ((int64_t)self / 32) * 32;
@@ -802,7 +1075,6 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
             DispF<P, CT>::get(pj, pi, g, dx, dy, dz, code);
             d2f = (float)f_fma<CT>(dz, dz, f_fma<CT>(dy, dy, dx * dx));
         }
-        // bitonic sort across lanes (ascending)
         for (int k = 2; k <= 32; k <<= 1)
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
                 float o = __shfl_xor_sync(0xffffffffu, d2f, jj);
@@ -814,7 +1086,6 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
         int kk = min(max(A.k_target / 4, 4), 30);
         float dk = __shfl_sync(0xffffffffu, d2f, kk);
         if (!(dk < INFINITY)) {
-            // fewer mates than needed: the largest finite one, else a mean-spacing guess
             float mx = d2f < INFINITY ? d2f : 0.f;
             mx = warp_max<float>(mx);
             if (mx > 0.f) dk = mx;
@@ -827,41 +1098,126 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
         rhi2 = (CT)dk * (CT)2.6;
     }
     CT rlo2 = 0;
-    CT cap2 = g.periodic ? (CT)(0.249 * fmin(g.L[0], fmin(g.L[1], g.L[2])) * fmin(g.L[0], fmin(g.L[1], g.L[2])))
+    const double lmin = fmin(g.L[0], fmin(g.L[1], g.L[2]));
+    CT cap2 = g.periodic ? (CT)(0.249 * lmin * lmin)
                          : (CT)(4.0 * (g.L[0] * g.L[0] + g.L[1] * g.L[1] + g.L[2] * g.L[2]));
     bool done = false;
+    bool need_exact = false, ovf = false;
     for (int pass = 0; pass < A.max_passes && !done; pass++) {
         cc.n_passes++;
         if (rhi2 > cap2) rhi2 = cap2;
         int cnt = -1;
-        for (int shrink = 0; shrink < 40; shrink++) {
-            cnt = collect<P, CT>(S, spos, A.N, g, A.tree, self, pi, rlo2, rhi2);
-            if (cnt == -2) return VT_ERR_CAPACITY;
-            if (cnt >= 0) break;
-            rhi2 = rlo2 + (rhi2 - rlo2) * (CT)0.5;
+        VT_T0(tc0);
+        for (int shrink = 0; shrink < 64; shrink++) {
+            cnt = collect<P, CT, TP>(S, spos, A.N, g, A.tree, self, pi, rlo2, rhi2, bmin, bmax);
+            cc.n_collect++;
+            if (cnt > 0) cc.n_collected += cnt;
+            if (cnt == -2) return CAP_STACK;
+            if (cnt <= K::CAND) break;
+            // too many: keep the largest prefix of histogram bins that fits (at least the first bin, narrowed
+            // again if needed)
+            __syncwarp();
+            int keep = 0, acc = 0;
+            for (int b = 0; b < HIST_BINS; b++) {
+                acc += (int)S.hist[b];
+                if (acc > K::CAND) break;
+                keep = b + 1;
+            }
+            unsigned long long blo = fbits<CT>(rlo2), bhi = fbits<CT>(rhi2);
+            unsigned long long nb = blo + (unsigned long long)((double)(bhi - blo) * (keep > 0 ? keep : 1) / HIST_BINS);
+            if (nb <= blo) nb = blo + 1;
+            if (nb >= bhi) return CAP_CAND;
+            rhi2 = fromfbits<CT>(nb);
+            cnt = -1;
         }
-        if (cnt < 0) return VT_ERR_CAPACITY;
+        if (cnt < 0 || cnt > K::CAND) return CAP_CAND;
         __syncwarp();
-        sort_cand<CT>(S, cnt);
-        // clip in increasing distance
-        for (int k = 0; k < cnt; k++) {
-            unsigned long long key = S.u.cand[k];
-            uint32_t j = (uint32_t)(key & 0xffffffffu);
-            float kf = __uint_as_float((uint32_t)(key >> 32));
-            if ((CT)kf * ((CT)1 - (CT)8 * u) > (CT)4 * R2) { done = true; break; }
-            P pj = spos[j];
-            CT dx, dy, dz;
-            int code;
-            DispF<P, CT>::get(pj, pi, g, dx, dy, dz, code);
+        VT_T1(cc, 0, tc0);
+        VT_T0(ts0);
+        sort_cand<CT, TP>(S, cnt);
+        VT_T1(cc, 1, ts0);
+        // candidates in batches of 32, one per lane, in increasing distance
+        for (int k0 = 0; k0 < cnt && !done; k0 += 32) {
+            const int k = k0 + (int)lane;
+            const bool valid = k < cnt;
+            CT dx = 0, dy = 0, dz = 0;
+            uint32_t j = 0;
+            int code = 13;
+            float kf = INFINITY;
+            if (valid) {
+                unsigned long long key = S.u.cd.key[k];
+                uint32_t slot = (uint32_t)(key & 0xffffffffu);
+                kf = __uint_as_float((uint32_t)(key >> 32));
+                j = S.u.cd.j[slot];
+                code = S.u.cd.code[slot];
+                dx = S.u.cd.dx[slot]; dy = S.u.cd.dy[slot]; dz = S.u.cd.dz[slot];
+            }
+            // security radius: a plane at |d| >= 2R cannot cut; keys only grow along the list
+            const bool far = valid && (CT)kf * ((CT)1 - (CT)8 * u) > (CT)4 * R2;
+            const unsigned farm = __ballot_sync(0xffffffffu, far);
+            const unsigned valm = __ballot_sync(0xffffffffu, valid);
+            const int nact = farm ? __ffs(farm) - 1 : __popc(valm);
+            const bool act = (int)lane < nact;
             CT d2 = f_fma<CT>(dz, dz, f_fma<CT>(dy, dy, dx * dx));
-            if (d2 == (CT)0) return VT_ERR_DUPLICATE;
-            CT h = (CT)0.5 * d2;
-            CT nrm = sqrt(d2);
-            cc.n_tested++;
-            int r = clip_plane<P, CT, EXACT>(S, T, np, dx, dy, dz, h, nrm, j, code, spos, g, self, xws, cc);
-            if (r < 0) return r;
-            if (r == 2) return RC_NEED_EXACT;
-            if (r == 1) R2 = rmax2<CT>(T);
+            if (__any_sync(0xffffffffu, act && d2 == (CT)0)) return VT_ERR_DUPLICATE;
+            const CT h = (CT)0.5 * d2;
+            const CT nrm = sqrt(d2);
+            const CT hb = (CT)16 * u * h;
+            unsigned outm[TP];
+#pragma unroll
+            for (int e = 0; e < TP; e++) outm[e] = 0u;
+            VT_T0(tt0);
+            if (nact > 0)
+                test_slots<P, CT, EXACT, TP>(S, C.vm, act, dx, dy, dz, h, nrm, hb, j, code, outm, spos, g, self, xws, cc,
+                                         need_exact, ovf);
+            if (!EXACT && __any_sync(0xffffffffu, need_exact)) return RC_NEED_EXACT;
+            if (EXACT && __any_sync(0xffffffffu, ovf)) return VT_ERR_NUMERIC;
+            cc.n_tested += nact;
+            VT_T1(cc, 2, tt0);
+            VT_T0(tk0);
+            // apply the cutting planes in order; the later ones are re-tested against the new vertices only
+            unsigned anyo = 0u;
+#pragma unroll
+            for (int e = 0; e < TP; e++) anyo |= outm[e];
+            unsigned cutm = __ballot_sync(0xffffffffu, act && anyo);
+            bool any_cut = cutm != 0;
+            while (cutm) {
+                const int L = __ffs(cutm) - 1;
+                unsigned rem[TP], newm[TP];
+#pragma unroll
+                for (int e = 0; e < TP; e++) rem[e] = __shfl_sync(0xffffffffu, outm[e], L);
+                CT px = __shfl_sync(0xffffffffu, dx, L), py = __shfl_sync(0xffffffffu, dy, L),
+                   pz = __shfl_sync(0xffffffffu, dz, L), ph = __shfl_sync(0xffffffffu, h, L),
+                   pn = __shfl_sync(0xffffffffu, nrm, L);
+                uint32_t pj = __shfl_sync(0xffffffffu, j, L);
+                int pc = __shfl_sync(0xffffffffu, code, L);
+                VT_T0(ta0);
+                int rc = apply_cut<CT, TP>(S, C, rem, px, py, pz, ph, pn, pj, pc, newm);
+                VT_T1(cc, 6, ta0);
+                if (rc) return rc;
+                cc.n_cut++;
+                const bool later = act && (int)lane > L;
+#pragma unroll
+                for (int e = 0; e < TP; e++) outm[e] &= ~rem[e];
+                VT_T0(tr0);
+                test_slots<P, CT, EXACT, TP>(S, newm, later, dx, dy, dz, h, nrm, hb, j, code, outm, spos, g, self, xws,
+                                         cc, need_exact, ovf);
+                VT_T1(cc, 7, tr0);
+                if (!EXACT && __any_sync(0xffffffffu, need_exact)) return RC_NEED_EXACT;
+                if (EXACT && __any_sync(0xffffffffu, ovf)) return VT_ERR_NUMERIC;
+                anyo = 0u;
+#pragma unroll
+                for (int e = 0; e < TP; e++) anyo |= outm[e];
+                cutm = __ballot_sync(0xffffffffu, later && anyo);
+            }
+            if (any_cut) {
+                VT_T0(tb0);
+                R2 = rmax2<CT, TP>(S, C);
+                cell_box<CT, TP>(S, C, bmin, bmax);
+                VT_T1(cc, 8, tb0);
+            }
+            VT_T1(cc, 3, tk0);
+            if (farm) done = true;  // the list reached |d| > 2R: certified
         }
         __syncwarp();
         if (done) break;
@@ -870,40 +1226,36 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
         // an ill-conditioned vertex (infinite error bound) blocks the certificate: redo the cell in FP64
         if (!EXACT && !(R2 < (CT)INFINITY)) return RC_NEED_EXACT;
         if (rhi2 >= cap2) return g.periodic ? VT_ERR_UNSUPPORTED : VT_ERR_SECURITY;
-        // next pass: the annulus up to 2R, but at most twice the radius
-        rlo2 = rhi2;
-        CT nxt = (CT)4 * R2 * ((CT)1 + (CT)32 * u);
-        rhi2 = nxt < rhi2 * (CT)4 ? nxt : rhi2 * (CT)4;
+        // next pass: the annulus up to 2R, at most twice the radius (policy 1: also no further than the radius
+        // that the density seen so far says holds about 3/4 of a pass's capacity)
+        {
+            CT nxt = (CT)4 * R2 * ((CT)1 + (CT)32 * u);
+            double rh = sqrt((double)rhi2), rl = sqrt((double)rlo2);
+            double shell = rh * rh * rh - rl * rl * rl;
+            double lim = 4.0 * (double)rhi2;
+            if (A.radius_policy == 1 && cnt > 0 && shell > 0.0) {
+                double r3 = rh * rh * rh + 0.75 * K::CAND * shell / (double)cnt;
+                double r = cbrt(r3);
+                lim = fmin(lim, fmax(r * r, 1.21 * (double)rhi2));
+            }
+            rlo2 = rhi2;
+            rhi2 = (double)nxt < lim ? nxt : (CT)lim;
+        }
     }
     if (!done) return (!EXACT && !(R2 < (CT)INFINITY)) ? RC_NEED_EXACT : VT_ERR_SECURITY;
-    if (g.periodic && !((CT)16 * R2 < (CT)(fmin(g.L[0], fmin(g.L[1], g.L[2])) * fmin(g.L[0], fmin(g.L[1], g.L[2])))))
-        return VT_ERR_UNSUPPORTED;
+    if (g.periodic && !((CT)16 * R2 < (CT)(lmin * lmin))) return VT_ERR_UNSUPPORTED;
 
-    // ---------------- emission: triangles and directed-edge hash into shared memory
+    // ---------------- emission: one triangle per plane present, then walks along the adjacency
     __syncwarp();
-    for (int k = (int)lane; k < HASH_SZ; k += 32) S.u.em.hash[k] = 0xffffffffu;
-    for (int k = (int)lane; k < MAXP; k += 32) S.u.em.first[k] = 0xffffffffu;
+    VT_T0(te0);
+    for (int k = (int)lane; k < K::MAXP; k += 32) S.u.em.first[k] = 0xffffffffu;
     __syncwarp();
 #pragma unroll
-    for (int e = 0; e < TPL; e++) {
-        if ((T.vm[e] >> lane) & 1u) {
+    for (int e = 0; e < TP; e++) {
+        if ((C.vm[e] >> lane) & 1u) {
             uint32_t t = e * 32 + lane;
-            uint32_t id = T.id[e];
-            S.u.em.tid[t] = id;
-            S.u.em.tx[t] = T.x[e]; S.u.em.ty[t] = T.y[e]; S.u.em.tz[t] = T.z[e];
-            uint32_t a = id & 255, b = (id >> 8) & 255, c = (id >> 16) & 255;
-            uint32_t keys[3] = {(a << 8) | b, (b << 8) | c, (c << 8) | a};
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                uint32_t key = keys[q];
-                uint32_t ent = (key << 8) | t;
-                uint32_t hsh = (key * 2654435761u) >> 23;
-                for (int probe = 0; probe < HASH_SZ; probe++) {
-                    uint32_t prev = atomicCAS(&S.u.em.hash[hsh], 0xffffffffu, ent);
-                    if (prev == 0xffffffffu) break;
-                    hsh = (hsh + 1) & (HASH_SZ - 1);
-                }
-            }
+            uint32_t a, b, c;
+            unpack<TP>(S.tid[t], a, b, c);
             atomicMin(&S.u.em.first[a], t);
             atomicMin(&S.u.em.first[b], t);
             atomicMin(&S.u.em.first[c], t);
@@ -916,7 +1268,7 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
         if (__any_sync(0xffffffffu, bad)) return VT_ERR_UNSUPPORTED;
     }
     // facets: lane (chunk c) walks plane c*32+lane; fan from the facet's first vertex
-    constexpr int PCH = MAXP / 32;
+    constexpr int PCH = K::MAXP / 32;
     double vol = 0.0, mzx = 0.0, mzy = 0.0, mzz = 0.0, m2 = 0.0;
     CT fA[PCH], fcx[PCH], fcy[PCH], fcz[PCH];
     bool fem[PCH];
@@ -924,21 +1276,21 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
     for (int c = 0; c < PCH; c++) {
         fem[c] = false;
         fA[c] = fcx[c] = fcy[c] = fcz[c] = (CT)0;
-        if (c * 32 >= np) continue;
+        if (c * 32 >= C.np) continue;
         int p = c * 32 + (int)lane;
-        bool present = p < np && S.u.em.first[p] != 0xffffffffu;
+        bool present = p < C.np && S.u.em.first[p] != 0xffffffffu;
         if (!present) continue;
         uint32_t t0 = S.u.em.first[p];
-        CT x0 = S.u.em.tx[t0], y0 = S.u.em.ty[t0], z0 = S.u.em.tz[t0];
+        CT x0 = S.tx[t0], y0 = S.ty[t0], z0 = S.tz[t0];
         CT inrm = (CT)1 / S.pnrm[p];
         CT nhx = S.pnx[p] * inrm, nhy = S.pny[p] * inrm, nhz = S.pnz[p] * inrm;
         CT A_ = 0, csx = 0, csy = 0, csz = 0, sm2 = 0;
-        uint32_t cur = succ_tri<CT>(S, t0, p);
-        for (int guard = 0; guard < MAXT && cur != 0xffffffffu; guard++) {
-            uint32_t nxt = succ_tri<CT>(S, cur, p);
-            if (nxt == t0 || nxt == 0xffffffffu) break;
-            CT x1 = S.u.em.tx[cur], y1 = S.u.em.ty[cur], z1 = S.u.em.tz[cur];
-            CT x2 = S.u.em.tx[nxt], y2 = S.u.em.ty[nxt], z2 = S.u.em.tz[nxt];
+        uint32_t cur = succ_tri<CT, TP>(S, t0, p);
+        for (int guard = 0; guard < K::MAXT && cur != t0; guard++) {
+            uint32_t nxt = succ_tri<CT, TP>(S, cur, p);
+            if (nxt == t0) break;
+            CT x1 = S.tx[cur], y1 = S.ty[cur], z1 = S.tz[cur];
+            CT x2 = S.tx[nxt], y2 = S.ty[nxt], z2 = S.tz[nxt];
             CT e1x = x1 - x0, e1y = y1 - y0, e1z = z1 - z0;
             CT e2x = x2 - x0, e2y = y2 - y0, e2z = z2 - z0;
             CT crx = f_fma<CT>(e1y, e2z, -e1z * e2y), cry = f_fma<CT>(e1z, e2x, -e1x * e2z),
@@ -1014,29 +1366,37 @@ __device__ int do_cell(WarpSmem<CT>& S, const ClipArgs& A, uint32_t self, double
         atomicMax(&A.st->max_faces, (unsigned)nf_total);
         atomicAdd(&A.st->n_faces, (unsigned long long)nf_total);
     }
+    VT_T1(cc, 4, te0);
     return 0;
 }
 
-template <typename P, typename CT, bool EXACT>
-__global__ void __launch_bounds__(CLIP_WARPS * 32) k_clip(ClipArgs A) {
+// Fast kernels: Cap<4>, CLIP_WARPS warps per block, every cell; cells they cannot finish (an undecided FP64
+// test, an ill-conditioned vertex or a capacity overflow) are appended to the exact list.
+// Exact kernel: Cap<16>, one warp per block, the listed cells, exact predicates.
+template <typename P, typename CT, bool EXACT, int TP, int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
-    WarpSmem<CT>& S = reinterpret_cast<WarpSmem<CT>*>(smem_raw)[w];
-    const int gw = blockIdx.x * CLIP_WARPS + w;
+    WarpSmem<CT, TP>& S = reinterpret_cast<WarpSmem<CT, TP>*>(smem_raw)[w];
+    const int gw = blockIdx.x * WPB + w;
     double* xws = EXACT ? (A.xws + (size_t)gw * EXACT_WS) : nullptr;
-    CellCounters cc = {0, 0, 0, 0, 0, 0};
+    CellCounters cc = {};
     const uint32_t total = EXACT ? 0u : (uint32_t)A.N;
     for (;;) {
         uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(EXACT ? &A.st->work_next_exact : &A.st->work_next, (unsigned)CHUNK);
+        const unsigned chunk = EXACT ? 1u : (unsigned)CHUNK;
+        if (lane == 0) base = atomicAdd(EXACT ? &A.st->work_next_exact : &A.st->work_next, chunk);
         base = __shfl_sync(0xffffffffu, base, 0);
         uint32_t lim = EXACT ? *((volatile unsigned*)&A.st->n_exact_cells) : total;
         if (base >= lim) break;
-        for (uint32_t q = base; q < base + CHUNK && q < lim; q++) {
+        for (uint32_t q = base; q < base + chunk && q < lim; q++) {
             uint32_t self = EXACT ? A.exact_list[q] : q;
-            int rc = do_cell<P, CT, EXACT>(S, A, self, xws, cc);
+            VT_T0(tall);
+            int rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc);
+            VT_T1(cc, 5, tall);
             __syncwarp();
+            if (!EXACT && rc <= -100) rc = RC_NEED_EXACT;  // capacity: the larger exact kernel takes the cell
             if (lane == 0) {
                 if (rc == 0) {
                     A.cstat[self] = CS_DONE;
@@ -1046,11 +1406,31 @@ __global__ void __launch_bounds__(CLIP_WARPS * 32) k_clip(ClipArgs A) {
                     A.exact_list[slot] = self;
                 } else {
                     A.cstat[self] = CS_ERROR;
-                    if (atomicCAS(&A.st->error, 0, rc) == 0) A.st->error_cell = (int)self;
+                    int code = rc <= -100 ? VT_ERR_CAPACITY : rc;
+                    if (atomicCAS(&A.st->error, 0, code) == 0) {
+                        A.st->error_cell = (int)self;
+                        A.st->error_detail = rc;
+                    }
                 }
             }
         }
     }
+    // n_fp64 / n_exact / n_zero are counted by the lanes that did the work; the others are warp-uniform
+    unsigned f64 = cc.n_fp64, xe = cc.n_exact, xz = cc.n_zero;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        f64 += __shfl_xor_sync(0xffffffffu, f64, o);
+        xe += __shfl_xor_sync(0xffffffffu, xe, o);
+        xz += __shfl_xor_sync(0xffffffffu, xz, o);
+    }
+    cc.n_fp64 = f64; cc.n_exact = xe; cc.n_zero = xz;
+#ifdef VT_PHASE_TIMERS
+    {
+        unsigned long long t9 = cc.t[9];
+        for (int o = 16; o; o >>= 1) t9 += __shfl_xor_sync(0xffffffffu, t9, o);
+        cc.t[9] = t9;
+    }
+#endif
     if (lane == 0) {
         atomicAdd(&A.st->n_cut, (unsigned long long)cc.n_cut);
         atomicAdd(&A.st->n_tested, (unsigned long long)cc.n_tested);
@@ -1058,6 +1438,11 @@ __global__ void __launch_bounds__(CLIP_WARPS * 32) k_clip(ClipArgs A) {
         atomicAdd(&A.st->n_fp64, (unsigned long long)cc.n_fp64);
         atomicAdd(&A.st->n_exact_preds, (unsigned long long)cc.n_exact);
         atomicAdd(&A.st->n_exact_zero, (unsigned long long)cc.n_zero);
+        atomicAdd(&A.st->n_collect, (unsigned long long)cc.n_collect);
+        atomicAdd(&A.st->n_collected, (unsigned long long)cc.n_collected);
+#ifdef VT_PHASE_TIMERS
+        for (int k = 0; k < 10; k++) atomicAdd(&A.st->t_phase[k], cc.t[k]);
+#endif
     }
 }
 
@@ -1066,13 +1451,15 @@ __global__ void __launch_bounds__(CLIP_WARPS * 32) k_clip(ClipArgs A) {
 namespace vt {
 template <typename P, typename CT, bool EXACT>
 static void launch_one(const ClipArgs& a, int sm_count, cudaStream_t s) {
-    size_t smem = sizeof(WarpSmem<CT>) * CLIP_WARPS;
-    cudaFuncSetAttribute(k_clip<P, CT, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int TP = EXACT ? 16 : 4;
+    constexpr int WPB = EXACT ? 1 : CLIP_WARPS;
+    size_t smem = sizeof(WarpSmem<CT, TP>) * WPB;
+    cudaFuncSetAttribute(k_clip<P, CT, EXACT, TP, WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip<P, CT, EXACT>, CLIP_WARPS * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip<P, CT, EXACT, TP, WPB>, WPB * 32, smem);
     if (per_sm < 1) per_sm = 1;
     int blocks = sm_count * per_sm;
-    if (EXACT) blocks = a.xws_warps / CLIP_WARPS;
-    k_clip<P, CT, EXACT><<<blocks, CLIP_WARPS * 32, smem, s>>>(a);
+    if (EXACT) blocks = a.xws_warps < blocks ? a.xws_warps : blocks;
+    k_clip<P, CT, EXACT, TP, WPB><<<blocks, WPB * 32, smem, s>>>(a);
 }
 }  // namespace vt

@@ -8,12 +8,8 @@
 namespace vt {
 
 constexpr int WARP = 32;
-constexpr int MAXT = 128;       // triangle (vertex) slots per cell: 4 per lane
-constexpr int TPL = MAXT / WARP;
-constexpr int MAXP = 128;       // planes that may cut one cell (ids are 8-bit)
-constexpr int CAND_CAP = 128;   // candidates per radius pass
-constexpr int STACK_CAP = 192;  // tree traversal stack per warp
-constexpr int HASH_SZ = 512;    // directed-edge hash for facet walking
+constexpr int STACK_CAP = 192;  // tree traversal stack per warp (fast clipping kernels)
+constexpr int MAX_FACETS = 510; // facets of one cell (the exact kernel's plane capacity minus the initial six)
 constexpr int BUCKET = 32;      // particles per leaf bucket of the search tree
 constexpr int MAX_LEVELS = 8;
 
@@ -32,6 +28,9 @@ struct DevStatus {
     unsigned long long n_exact_preds;
     unsigned long long n_exact_zero;
     unsigned long long face_next;    // next free facet record
+    unsigned long long n_collect;    // candidate collections (tree traversals)
+    unsigned long long n_collected;  // candidates collected
+    unsigned long long t_phase[10];  // optional phase cycle counters (VT_PHASE_TIMERS builds)
     unsigned int n_exact_cells;      // length of the exact-recompute list
     unsigned int max_faces;
     int error;                       // first VT_ERR_* (atomicCAS from 0)
@@ -39,7 +38,8 @@ struct DevStatus {
     unsigned int work_next;          // dynamic cell scheduler
     unsigned int work_next_exact;
     unsigned int invalid_input;      // count of NaN / out-of-box coordinates
-    unsigned int pad;
+    int error_detail;                // internal reason of the first error (capacity: -101 planes, -102 triangles,
+                                     // -103 boundary, -104 candidates, -105 search stack)
 };
 
 // facet record (one per cell side of a facet between two particles)
@@ -114,4 +114,7 @@ struct vt_handle_s {
     vt::DevStatus hstat;    // host copy after build
     int64_t n_faces;
     int sm_count;
+    int64_t n_launches;
+    double t_sort_ms, t_clip_ms;
+    cudaEvent_t ev[4];
 };

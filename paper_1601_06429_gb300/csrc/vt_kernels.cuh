@@ -14,16 +14,16 @@ struct __align__(32) dpt4 {
 
 size_t scan_tmp_bytes(int64_t n);
 size_t radix_tmp_bytes(int64_t N);
-void scan_u32_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp, cudaStream_t s);
-void scan_u16_i64(const uint16_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
-void radix_sort(uint64_t* key, uint32_t* val, uint64_t* key_alt, uint32_t* val_alt, int64_t N, int bits, void* tmp,
+int scan_u32_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp, cudaStream_t s);
+int scan_u16_i64(const uint16_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
+int radix_sort(uint64_t* key, uint32_t* val, uint64_t* key_alt, uint32_t* val_alt, int64_t N, int bits, void* tmp,
                 cudaStream_t s);
-void launch_key(const void* pos, int dtype, int64_t N, const Geometry& g, uint64_t* key, uint32_t* idx, DevStatus* st,
+int launch_key(const void* pos, int dtype, int64_t N, const Geometry& g, uint64_t* key, uint32_t* idx, DevStatus* st,
                 cudaStream_t s);
-void launch_gather(const void* pos, const void* mass, int dtype, const uint32_t* perm, int64_t N, void* spos,
+int launch_gather(const void* pos, const void* mass, int dtype, const uint32_t* perm, int64_t N, void* spos,
                    uint32_t* inv, cudaStream_t s);
 void tree_layout(int64_t N, Tree& t);
-void launch_tree(const void* spos, int dtype, int64_t N, Tree& t, cudaStream_t s);
+int launch_tree(const void* spos, int dtype, int64_t N, Tree& t, cudaStream_t s);
 
 // clipping (vt_clip.cu)
 struct ClipArgs {
@@ -33,6 +33,7 @@ struct ClipArgs {
     Tree tree;
     int k_target;
     int max_passes;
+    int radius_policy;  // 0: radius doubling; 1: next pass also limited by the density seen so far
     CellOut* cell;
     uint32_t* face_start;
     uint16_t* face_count;
@@ -44,22 +45,24 @@ struct ClipArgs {
     double* xws;   // exact workspace, per warp
     int xws_warps;
 };
-void launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s);
-void launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
+int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s);
+int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
 size_t exact_ws_doubles_per_warp();
 
 // post-processing (vt_post.cu)
-void launch_out_vol(const CellOut* cell, const uint32_t* perm, int64_t N, void* vol, int dtype, cudaStream_t s);
-void launch_density(const CellOut* cell, const void* spos, int dtype, const uint32_t* perm, int64_t N,
+int launch_out_vol(const CellOut* cell, const uint32_t* perm, int64_t N, void* vol, int dtype, cudaStream_t s);
+int launch_density(const CellOut* cell, const void* spos, int dtype, const uint32_t* perm, int64_t N,
                     double* dens_sorted, void* dens, cudaStream_t s);
-void launch_nbr_count(const uint16_t* face_count, const uint32_t* inv, int64_t N, uint16_t* cnt_in, cudaStream_t s);
-void launch_nbr_emit(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const uint32_t* perm,
+int launch_nbr_count(const uint16_t* face_count, const uint32_t* inv, int64_t N, uint16_t* cnt_in, cudaStream_t s);
+int launch_nbr_emit(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const uint32_t* perm,
                      const uint32_t* inv, const int64_t* nbr_off, int64_t N, int32_t* nbr_id, cudaStream_t s);
-void launch_gradient(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const double* dens_sorted,
+int launch_gradient(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const double* dens_sorted,
                      const uint32_t* perm, int64_t N, void* grad, int dtype, cudaStream_t s);
-void launch_grid(const void* spos, int dtype, int64_t N, const Geometry& g, const Tree& t, const double* dens_sorted,
-                 const uint32_t* perm, int G, int S, void* grid, DevStatus* st, int sm_count, cudaStream_t s);
-void launch_backward(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const CellOut* cell,
+int launch_grid(const void* spos, int dtype, int64_t N, const Geometry& g, const Face* faces,
+                const uint32_t* face_start, const uint16_t* face_count, const uint64_t* keys,
+                const double* dens_sorted, const uint32_t* perm, int G, int S, void* grid, DevStatus* st,
+                cudaStream_t s);
+int launch_backward(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const CellOut* cell,
                      const void* spos, int dtype, const uint32_t* perm, const uint32_t* inv, int64_t N,
                      const void* dLdV, double dLdE, void* out, cudaStream_t s);
 

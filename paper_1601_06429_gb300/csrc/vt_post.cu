@@ -23,10 +23,11 @@ __global__ void k_out_vol(const CellOut* __restrict__ cell, const uint32_t* __re
     if (k < N) vol[perm[k]] = (T)cell[k].vol;
 }
 
-void launch_out_vol(const CellOut* cell, const uint32_t* perm, int64_t N, void* vol, int dtype, cudaStream_t s) {
+int launch_out_vol(const CellOut* cell, const uint32_t* perm, int64_t N, void* vol, int dtype, cudaStream_t s) {
     unsigned nb = (unsigned)((N + 255) / 256);
     if (dtype == VT_F32) k_out_vol<float><<<nb, 256, 0, s>>>(cell, perm, N, (float*)vol);
     else k_out_vol<double><<<nb, 256, 0, s>>>(cell, perm, N, (double*)vol);
+    return 1;
 }
 
 // Implementation section: density = particle mass / cell volume
@@ -41,7 +42,7 @@ __global__ void k_density(const CellOut* __restrict__ cell, const P* __restrict_
     if (dens) dens[perm[k]] = (T)d;
 }
 
-void launch_density(const CellOut* cell, const void* spos, int dtype, const uint32_t* perm, int64_t N,
+int launch_density(const CellOut* cell, const void* spos, int dtype, const uint32_t* perm, int64_t N,
                     double* dens_sorted, void* dens, cudaStream_t s) {
     unsigned nb = (unsigned)((N + 255) / 256);
     if (dtype == VT_F32)
@@ -50,6 +51,7 @@ void launch_density(const CellOut* cell, const void* spos, int dtype, const uint
     else
         k_density<dpt4, double><<<nb, 256, 0, s>>>(cell, (const dpt4*)spos, perm, N, dens_sorted,
                                                     (double*)dens);
+    return 1;
 }
 
 // ------------------------------------------------------------------ neighbour lists
@@ -59,8 +61,9 @@ __global__ void k_nbr_count(const uint16_t* __restrict__ face_count, const uint3
     if (i < N) cnt_in[i] = face_count[inv[i]];
 }
 
-void launch_nbr_count(const uint16_t* face_count, const uint32_t* inv, int64_t N, uint16_t* cnt_in, cudaStream_t s) {
+int launch_nbr_count(const uint16_t* face_count, const uint32_t* inv, int64_t N, uint16_t* cnt_in, cudaStream_t s) {
     k_nbr_count<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(face_count, inv, N, cnt_in);
+    return 1;
 }
 
 // one warp per particle (input order): its facets' neighbours mapped to input indices, sorted ascending
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_nbr_emit(const Face* __rest
                                                               const uint32_t* __restrict__ inv,
                                                               const int64_t* __restrict__ nbr_off, int64_t N,
                                                               int32_t* __restrict__ nbr_id) {
-    __shared__ uint32_t buf[EMIT_WARPS][MAXP];
+    __shared__ uint32_t buf[EMIT_WARPS][512];
     const int w = threadIdx.x >> 5;
     const unsigned lane = threadIdx.x & 31;
     int64_t i = (int64_t)blockIdx.x * EMIT_WARPS + w;
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_nbr_emit(const Face* __rest
         return;
     }
     int m = 64;
-    while (m < cnt) m <<= 1;
+    while (m < cnt) m <<= 1;  // cnt <= MAX_FACETS < 512
     for (int q = lane; q < m; q += 32) buf[w][q] = q < cnt ? perm[faces[st + q].nbr] : 0xffffffffu;
     __syncwarp();
     for (int kk = 2; kk <= m; kk <<= 1)
@@ -113,10 +116,11 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_nbr_emit(const Face* __rest
     for (int q = lane; q < cnt; q += 32) nbr_id[o + q] = (int32_t)buf[w][q];
 }
 
-void launch_nbr_emit(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const uint32_t* perm,
+int launch_nbr_emit(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const uint32_t* perm,
                      const uint32_t* inv, const int64_t* nbr_off, int64_t N, int32_t* nbr_id, cudaStream_t s) {
     unsigned nb = (unsigned)((N + EMIT_WARPS - 1) / EMIT_WARPS);
     k_nbr_emit<<<nb, EMIT_WARPS * 32, 0, s>>>(faces, face_start, face_count, perm, inv, nbr_off, N, nbr_id);
+    return 1;
 }
 
 // ------------------------------------------------------------------ density gradient
@@ -157,7 +161,7 @@ __global__ void k_gradient(const Face* __restrict__ faces, const uint32_t* __res
     grad[3 * (int64_t)i + 2] = (T)gz;
 }
 
-void launch_gradient(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const double* dens_sorted,
+int launch_gradient(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const double* dens_sorted,
                      const uint32_t* perm, int64_t N, void* grad, int dtype, cudaStream_t s) {
     unsigned nb = (unsigned)((N + 255) / 256);
     if (dtype == VT_F32)
@@ -166,21 +170,21 @@ void launch_gradient(const Face* faces, const uint32_t* face_start, const uint16
     else
         k_gradient<double><<<nb, 256, 0, s>>>(faces, face_start, face_count, dens_sorted, perm, N,
                                               (double*)grad);
+    return 1;
 }
 
 // ------------------------------------------------------------------ grid densities
 // Implementation section ("average Voronoi densities on a regular grid"); reading: the density of the cell
-// containing each of the node's S^3 sub-points (its nearest particle), averaged.  The nearest particle is
-// decided in FP64 with the fixed evaluation order fma(dz,dz, fma(dy,dy, dx*dx)) on minimum-image dx, ties to
-// the lower input index; FP32 is only used to prune.
-__device__ __forceinline__ float gap1(float q, float lo, float hi, float L, int periodic) {
-    float d = fmaxf(fmaxf(lo - q, q - hi), 0.f);
-    if (periodic) {
-        d = fminf(d, fmaxf(lo + L - q, 0.f));
-        d = fminf(d, fmaxf(q + L - hi, 0.f));
-    }
-    return d;
-}
+// containing each of the node's S^3 sub-points (its nearest particle), averaged.
+// The nearest particle is found by a greedy walk on the Voronoi neighbour graph (a site that is not the
+// nearest always has a strictly nearer Voronoi neighbour), started from the previous node's answer or from
+// the Morton-order position of the sub-point, first in FP32 and then confirmed in FP64 with the fixed
+// evaluation order fma(dz,dz, fma(dy,dy, dx*dx)) on minimum-image dx, ties to the lower input index.
+struct GridConst {
+    double fu[8];   // (u + 1/2) / S
+    double h[3];    // L / G per axis
+};
+
 __device__ __forceinline__ double wrap_d(double t, double L, int periodic) {
     if (periodic) {
         if (t > 0.5 * L) t = __dsub_rn(t, L);
@@ -188,150 +192,141 @@ __device__ __forceinline__ double wrap_d(double t, double L, int periodic) {
     }
     return t;
 }
-
-constexpr int GRID_WARPS = 4;
-constexpr int GSTACK = 192;
-
-template <typename P>
-__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(const P* __restrict__ spos, int64_t N, Geometry g, Tree t,
-                                                           const double* __restrict__ dens,
-                                                           const uint32_t* __restrict__ perm, int G, int S,
-                                                           void* __restrict__ out, int dtype, DevStatus* st) {
-    __shared__ uint32_t stack[GRID_WARPS][GSTACK];
-    const int w = threadIdx.x >> 5;
-    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-    const int S3 = S * S * S;
-    const int64_t gw = (int64_t)blockIdx.x * GRID_WARPS + w, nw = (int64_t)gridDim.x * GRID_WARPS;
-    const float slack = 4.0f * 1.2e-7f *
-                        fmaxf(fmaxf(fabsf(g.hif[0]), fabsf(g.lof[0])),
-                              fmaxf(fmaxf(fabsf(g.hif[1]), fabsf(g.lof[1])), fmaxf(fabsf(g.hif[2]), fabsf(g.lof[2]))));
-    uint32_t guess = 0;  // sorted index of the last answer (spatial coherence along rows)
-    // each warp takes whole rows of G nodes along x
-    for (int64_t row = gw; row < (int64_t)G * G; row += nw) {
-        for (int a = 0; a < G; a++) {
-            int64_t node = row * G + a;
-            int b = (int)(row % G), c = (int)(row / G);
-            double acc = 0.0;
-            for (int sp = 0; sp < S3; sp++) {
-                int uu = sp % S, vv = (sp / S) % S, ww = sp / (S * S);
-                double qd[3];
-                qd[0] = __dadd_rn(g.lo[0], __dmul_rn(__dadd_rn((double)a, __ddiv_rn(__dadd_rn((double)uu, 0.5), (double)S)),
-                                                     __ddiv_rn(g.L[0], (double)G)));
-                qd[1] = __dadd_rn(g.lo[1], __dmul_rn(__dadd_rn((double)b, __ddiv_rn(__dadd_rn((double)vv, 0.5), (double)S)),
-                                                     __ddiv_rn(g.L[1], (double)G)));
-                qd[2] = __dadd_rn(g.lo[2], __dmul_rn(__dadd_rn((double)c, __ddiv_rn(__dadd_rn((double)ww, 0.5), (double)S)),
-                                                     __ddiv_rn(g.L[2], (double)G)));
-                float qx = (float)qd[0], qy = (float)qd[1], qz = (float)qd[2];
-                // initial bound from the previous answer
-                double best;
-                uint32_t bj = guess, bi;
-                {
-                    P pj = spos[bj];
-                    double dx = wrap_d(__dsub_rn((double)pj.x, qd[0]), g.L[0], g.periodic);
-                    double dy = wrap_d(__dsub_rn((double)pj.y, qd[1]), g.L[1], g.periodic);
-                    double dz = wrap_d(__dsub_rn((double)pj.z, qd[2]), g.L[2], g.periodic);
-                    best = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
-                    bi = perm[bj];
-                }
-                float bestf = (float)best * 1.0001f + 1e-30f;
-                int top = t.levels;
-                int spn = 0;
-                {
-                    bool hit = false;
-                    if ((int64_t)lane < t.count[top]) {
-                        float4 lo = t.lo[t.off[top] + lane], hi = t.hi[t.off[top] + lane];
-                        float dx = fmaxf(gap1(qx, lo.x, hi.x, g.Lf[0], g.periodic) - slack, 0.f);
-                        float dy = fmaxf(gap1(qy, lo.y, hi.y, g.Lf[1], g.periodic) - slack, 0.f);
-                        float dz = fmaxf(gap1(qz, lo.z, hi.z, g.Lf[2], g.periodic) - slack, 0.f);
-                        hit = dx * dx + dy * dy + dz * dz <= bestf;
-                    }
-                    unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (hit) stack[w][__popc(m & lt)] = ((uint32_t)top << 27) | lane;
-                    spn = __popc(m);
-                }
-                __syncwarp();
-                while (spn > 0) {
-                    uint32_t ent = stack[w][spn - 1];
-                    spn--;
-                    __syncwarp();
-                    int lvl = ent >> 27;
-                    int64_t nd = ent & ((1u << 27) - 1);
-                    if (lvl == 1) {
-                        int64_t j = nd * 32 + lane;
-                        double d2 = INFINITY;
-                        uint32_t ji = 0xffffffffu;
-                        if (j < N) {
-                            P pj = spos[j];
-                            float fx = fabsf((float)pj.x - qx), fy = fabsf((float)pj.y - qy), fz = fabsf((float)pj.z - qz);
-                            if (g.periodic) {
-                                fx = fminf(fx, g.Lf[0] - fx); fy = fminf(fy, g.Lf[1] - fy); fz = fminf(fz, g.Lf[2] - fz);
-                            }
-                            // each float component is within `slack` of its FP64 value
-                            float df = sqrtf(fx * fx + fy * fy + fz * fz);
-                            if (df <= sqrtf(bestf) + 4.f * slack) {
-                                double dx = wrap_d(__dsub_rn((double)pj.x, qd[0]), g.L[0], g.periodic);
-                                double dy = wrap_d(__dsub_rn((double)pj.y, qd[1]), g.L[1], g.periodic);
-                                double dz = wrap_d(__dsub_rn((double)pj.z, qd[2]), g.L[2], g.periodic);
-                                d2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
-                                ji = perm[j];
-                            }
-                        }
-                        // warp argmin over (d2, input index)
-                        double md = d2;
-                        uint32_t mi = ji, ms = (uint32_t)j;
-#pragma unroll
-                        for (int o = 16; o; o >>= 1) {
-                            double od = __shfl_xor_sync(0xffffffffu, md, o);
-                            uint32_t oi = __shfl_xor_sync(0xffffffffu, mi, o);
-                            uint32_t os = __shfl_xor_sync(0xffffffffu, ms, o);
-                            if (od < md || (od == md && oi < mi)) { md = od; mi = oi; ms = os; }
-                        }
-                        if (md < best || (md == best && mi < bi)) {
-                            best = md; bi = mi; bj = ms;
-                            bestf = (float)best * 1.0001f + 1e-30f;
-                        }
-                    } else {
-                        int cl = lvl - 1;
-                        int64_t ch = nd * 32 + lane;
-                        bool hit = false;
-                        if (ch < t.count[cl]) {
-                            float4 lo = t.lo[t.off[cl] + ch], hi = t.hi[t.off[cl] + ch];
-                            float dx = fmaxf(gap1(qx, lo.x, hi.x, g.Lf[0], g.periodic) - slack, 0.f);
-                            float dy = fmaxf(gap1(qy, lo.y, hi.y, g.Lf[1], g.periodic) - slack, 0.f);
-                            float dz = fmaxf(gap1(qz, lo.z, hi.z, g.Lf[2], g.periodic) - slack, 0.f);
-                            hit = dx * dx + dy * dy + dz * dz <= bestf;
-                        }
-                        unsigned m = __ballot_sync(0xffffffffu, hit);
-                        if (spn + __popc(m) > GSTACK) {
-                            if (lane == 0) atomicCAS(&st->error, 0, VT_ERR_CAPACITY);
-                            break;
-                        }
-                        if (hit) stack[w][spn + __popc(m & lt)] = ((uint32_t)cl << 27) | (uint32_t)ch;
-                        spn += __popc(m);
-                        __syncwarp();
-                    }
-                }
-                guess = bj;
-                acc += dens[bj];
-            }
-            if (lane == 0) {
-                double v = acc / S3;
-                if (dtype == VT_F32) ((float*)out)[node] = (float)v;
-                else ((double*)out)[node] = v;
-            }
-        }
+__device__ __forceinline__ float wrap_f(float t, float L, int periodic) {
+    if (periodic) {
+        if (t > 0.5f * L) t -= L;
+        else if (t < -0.5f * L) t += L;
     }
+    return t;
+}
+__device__ __forceinline__ uint64_t spread16(uint32_t v) {
+    uint64_t x = v & 0xFFFFu;
+    x = (x | (x << 16)) & 0x0000FF0000FFull;
+    x = (x | (x << 8)) & 0x00F00F00F00Full;
+    x = (x | (x << 4)) & 0x0C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x249249249249ull;
+    return x;
 }
 
-void launch_grid(const void* spos, int dtype, int64_t N, const Geometry& g, const Tree& t, const double* dens_sorted,
-                 const uint32_t* perm, int G, int S, void* grid, DevStatus* st, int sm_count, cudaStream_t s) {
-    int blocks = sm_count * 8;
+constexpr int GRID_RUN = 8;
+
+template <typename P>
+__global__ void __launch_bounds__(256) k_grid(const P* __restrict__ spos, int64_t N, Geometry g,
+                                              const Face* __restrict__ faces, const uint32_t* __restrict__ face_start,
+                                              const uint16_t* __restrict__ face_count,
+                                              const uint64_t* __restrict__ keys, const double* __restrict__ dens,
+                                              const uint32_t* __restrict__ perm, int G, int S, GridConst gc,
+                                              void* __restrict__ out, int dtype, DevStatus* st) {
+    const int seg_per_row = (G + GRID_RUN - 1) / GRID_RUN;
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (int64_t)G * G * seg_per_row) return;
+    const int64_t row = tid / seg_per_row;
+    const int a0 = (int)(tid % seg_per_row) * GRID_RUN;
+    const int b = (int)(row % G), c = (int)(row / G);
+    const int S3 = S * S * S;
+    int64_t cur = -1;
+    for (int a = a0; a < min(a0 + GRID_RUN, G); a++) {
+        double acc = 0.0;
+        for (int sp = 0; sp < S3; sp++) {
+            const int uu = sp % S, vv = (sp / S) % S, ww = sp / (S * S);
+            double q[3];
+            q[0] = __dadd_rn(g.lo[0], __dmul_rn(__dadd_rn((double)a, gc.fu[uu]), gc.h[0]));
+            q[1] = __dadd_rn(g.lo[1], __dmul_rn(__dadd_rn((double)b, gc.fu[vv]), gc.h[1]));
+            q[2] = __dadd_rn(g.lo[2], __dmul_rn(__dadd_rn((double)c, gc.fu[ww]), gc.h[2]));
+            if (cur < 0) {
+                // Morton position of q in the sorted keys
+                uint32_t qi[3];
+                for (int k = 0; k < 3; k++) {
+                    double t = (q[k] - g.lo[k]) / g.L[k] * 65536.0;
+                    int v = (int)t;
+                    qi[k] = (uint32_t)min(max(v, 0), 65535);
+                }
+                uint64_t key = spread16(qi[0]) | (spread16(qi[1]) << 1) | (spread16(qi[2]) << 2);
+                int64_t lo = 0, hi = N;
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if (keys[mid] < key) lo = mid + 1;
+                    else hi = mid;
+                }
+                cur = lo < N ? lo : N - 1;
+            }
+            const float qf0 = (float)q[0], qf1 = (float)q[1], qf2 = (float)q[2];
+            // FP32 greedy walk
+            {
+                P pc = spos[cur];
+                float dx = wrap_f((float)pc.x - qf0, g.Lf[0], g.periodic);
+                float dy = wrap_f((float)pc.y - qf1, g.Lf[1], g.periodic);
+                float dz = wrap_f((float)pc.z - qf2, g.Lf[2], g.periodic);
+                float dbest = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                for (int step = 0; step < 100000; step++) {
+                    int64_t best = cur;
+                    uint32_t fs = face_start[cur];
+                    int fc = face_count[cur];
+                    for (int f = 0; f < fc; f++) {
+                        uint32_t jn = faces[fs + f].nbr;
+                        P pj = spos[jn];
+                        float ex = wrap_f((float)pj.x - qf0, g.Lf[0], g.periodic);
+                        float ey = wrap_f((float)pj.y - qf1, g.Lf[1], g.periodic);
+                        float ez = wrap_f((float)pj.z - qf2, g.Lf[2], g.periodic);
+                        float d = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+                        if (d < dbest) { dbest = d; best = jn; }
+                    }
+                    if (best == cur) break;
+                    cur = best;
+                }
+            }
+            // FP64 confirmation (same formula and tie rule as a brute-force argmin)
+            {
+                P pc = spos[cur];
+                double dx = wrap_d(__dsub_rn((double)pc.x, q[0]), g.L[0], g.periodic);
+                double dy = wrap_d(__dsub_rn((double)pc.y, q[1]), g.L[1], g.periodic);
+                double dz = wrap_d(__dsub_rn((double)pc.z, q[2]), g.L[2], g.periodic);
+                double dbest = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+                uint32_t ibest = perm[cur];
+                for (int step = 0; step < 100000; step++) {
+                    int64_t best = cur;
+                    uint32_t fs = face_start[cur];
+                    int fc = face_count[cur];
+                    for (int f = 0; f < fc; f++) {
+                        uint32_t jn = faces[fs + f].nbr;
+                        P pj = spos[jn];
+                        double ex = wrap_d(__dsub_rn((double)pj.x, q[0]), g.L[0], g.periodic);
+                        double ey = wrap_d(__dsub_rn((double)pj.y, q[1]), g.L[1], g.periodic);
+                        double ez = wrap_d(__dsub_rn((double)pj.z, q[2]), g.L[2], g.periodic);
+                        double d = __fma_rn(ez, ez, __fma_rn(ey, ey, __dmul_rn(ex, ex)));
+                        uint32_t ij = perm[jn];
+                        if (d < dbest || (d == dbest && ij < ibest)) { dbest = d; ibest = ij; best = jn; }
+                    }
+                    if (best == cur) break;
+                    cur = best;
+                }
+            }
+            acc += dens[cur];
+        }
+        const int64_t node = row * G + a;
+        const double v = acc / S3;
+        if (dtype == VT_F32) ((float*)out)[node] = (float)v;
+        else ((double*)out)[node] = v;
+    }
+    (void)st;
+}
+
+int launch_grid(const void* spos, int dtype, int64_t N, const Geometry& g, const Face* faces,
+                const uint32_t* face_start, const uint16_t* face_count, const uint64_t* keys,
+                const double* dens_sorted, const uint32_t* perm, int G, int S, void* grid, DevStatus* st,
+                cudaStream_t s) {
+    GridConst gc;
+    for (int u = 0; u < 8; u++) gc.fu[u] = ((double)u + 0.5) / (double)S;
+    for (int k = 0; k < 3; k++) gc.h[k] = g.L[k] / (double)G;
+    int64_t threads = (int64_t)G * G * ((G + GRID_RUN - 1) / GRID_RUN);
+    unsigned nb = (unsigned)((threads + 255) / 256);
     if (dtype == VT_F32)
-        k_grid<float4><<<blocks, GRID_WARPS * 32, 0, s>>>((const float4*)spos, N, g, t, dens_sorted,
-                                                          perm, G, S, grid, dtype, st);
+        k_grid<float4><<<nb, 256, 0, s>>>((const float4*)spos, N, g, faces, face_start, face_count, keys,
+                                          dens_sorted, perm, G, S, gc, grid, dtype, st);
     else
-        k_grid<dpt4><<<blocks, GRID_WARPS * 32, 0, s>>>((const dpt4*)spos, N, g, t, dens_sorted, perm,
-                                                        G, S, grid, dtype, st);
+        k_grid<dpt4><<<nb, 256, 0, s>>>((const dpt4*)spos, N, g, faces, face_start, face_count, keys, dens_sorted,
+                                        perm, G, S, gc, grid, dtype, st);
+    return 1;
 }
 
 // ------------------------------------------------------------------ backward
@@ -368,7 +363,7 @@ __global__ void k_backward(const Face* __restrict__ faces, const uint32_t* __res
     out[3 * (int64_t)i + 2] = az;
 }
 
-void launch_backward(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const CellOut* cell,
+int launch_backward(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const CellOut* cell,
                      const void* spos, int dtype, const uint32_t* perm, const uint32_t* inv, int64_t N,
                      const void* dLdV, double dLdE, void* out, cudaStream_t s) {
     (void)spos; (void)inv;
@@ -379,6 +374,7 @@ void launch_backward(const Face* faces, const uint32_t* face_start, const uint16
     else
         k_backward<double><<<nb, 256, 0, s>>>(faces, face_start, face_count, cell, perm, N, (const double*)dLdV, dLdE,
                                               (double*)out);
+    return 1;
 }
 
 }  // namespace vt

@@ -110,24 +110,25 @@ size_t scan_tmp_bytes(int64_t n) {
 }
 
 template <typename TI, typename TO>
-static void scan_rec(const TI* in, TO* out, int64_t n, char* tmp, cudaStream_t s) {
+static int scan_rec(const TI* in, TO* out, int64_t n, char* tmp, cudaStream_t s) {
     int64_t nb = (n + 4095) / 4096;
     if (nb <= 1) {
         k_scan_block<TI, TO><<<1, 1024, 0, s>>>(in, out, n, (TO*)nullptr);
-        return;
+        return 1;
     }
     TO* part = (TO*)tmp;
     char* rest = tmp + ((nb + 1) * sizeof(TO) + 15) / 16 * 16;
     k_scan_block<TI, TO><<<(unsigned)nb, 1024, 0, s>>>(in, out, n, part);
-    scan_rec<TO, TO>(part, part, nb, rest, s);
+    int k = scan_rec<TO, TO>(part, part, nb, rest, s);
     k_scan_add<TO><<<(unsigned)nb, 1024, 0, s>>>(out, n, part);
+    return k + 2;
 }
 
-void scan_u32_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp, cudaStream_t s) {
-    scan_rec<uint32_t, uint32_t>(in, out, n, (char*)tmp, s);
+int scan_u32_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp, cudaStream_t s) {
+    return scan_rec<uint32_t, uint32_t>(in, out, n, (char*)tmp, s);
 }
-void scan_u16_i64(const uint16_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s) {
-    scan_rec<uint16_t, int64_t>(in, out, n, (char*)tmp, s);
+int scan_u16_i64(const uint16_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s) {
+    return scan_rec<uint16_t, int64_t>(in, out, n, (char*)tmp, s);
 }
 
 // ---------------------------------------------------------------- radix sort
@@ -209,10 +210,11 @@ size_t radix_tmp_bytes(int64_t N) {
 }
 
 // sorts (key, val) by the low `bits` bits of key; the result ends in key/val
-void radix_sort(uint64_t* key, uint32_t* val, uint64_t* key_alt, uint32_t* val_alt, int64_t N, int bits, void* tmp,
-                cudaStream_t s) {
+int radix_sort(uint64_t* key, uint32_t* val, uint64_t* key_alt, uint32_t* val_alt, int64_t N, int bits, void* tmp,
+               cudaStream_t s) {
     int nb = (int)((N + RS_TILE - 1) / RS_TILE);
-    if (nb == 0) return;
+    if (nb == 0) return 0;
+    int launches = 0;
     uint32_t* hist = (uint32_t*)tmp;
     uint32_t* goff = hist + (size_t)nb * 256;
     void* stmp = goff + (size_t)nb * 256;
@@ -224,7 +226,7 @@ void radix_sort(uint64_t* key, uint32_t* val, uint64_t* key_alt, uint32_t* val_a
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
         k_radix_hist<<<nb, 256, 0, s>>>(ka, N, shift, hist, nb);
-        scan_u32_u32(hist, goff, (int64_t)nb * 256, stmp, s);
+        launches += 2 + scan_u32_u32(hist, goff, (int64_t)nb * 256, stmp, s);
         k_radix_scatter<<<nb, 256, 0, s>>>(ka, va, kb, vb, N, shift, goff, nb);
         uint64_t* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
@@ -233,6 +235,7 @@ void radix_sort(uint64_t* key, uint32_t* val, uint64_t* key_alt, uint32_t* val_a
         cudaMemcpyAsync(key, ka, N * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(val, va, N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     }
+    return launches;
 }
 
 // ---------------------------------------------------------------- gather
@@ -254,22 +257,24 @@ __global__ void k_gather(const T* __restrict__ pos, const T* __restrict__ mass, 
 template __global__ void k_key<float>(const float*, int64_t, Geometry, uint64_t*, uint32_t*, DevStatus*);
 template __global__ void k_key<double>(const double*, int64_t, Geometry, uint64_t*, uint32_t*, DevStatus*);
 
-void launch_key(const void* pos, int dtype, int64_t N, const Geometry& g, uint64_t* key, uint32_t* idx, DevStatus* st,
-                cudaStream_t s) {
+int launch_key(const void* pos, int dtype, int64_t N, const Geometry& g, uint64_t* key, uint32_t* idx, DevStatus* st,
+               cudaStream_t s) {
     unsigned nb = (unsigned)((N + 255) / 256);
     if (dtype == VT_F32)
         k_key<float><<<nb, 256, 0, s>>>((const float*)pos, N, g, key, idx, st);
     else
         k_key<double><<<nb, 256, 0, s>>>((const double*)pos, N, g, key, idx, st);
+    return 1;
 }
 
-void launch_gather(const void* pos, const void* mass, int dtype, const uint32_t* perm, int64_t N, void* spos,
-                   uint32_t* inv, cudaStream_t s) {
+int launch_gather(const void* pos, const void* mass, int dtype, const uint32_t* perm, int64_t N, void* spos,
+                  uint32_t* inv, cudaStream_t s) {
     unsigned nb = (unsigned)((N + 255) / 256);
     if (dtype == VT_F32)
         k_gather<float, float4><<<nb, 256, 0, s>>>((const float*)pos, (const float*)mass, perm, N, (float4*)spos, inv);
     else
         k_gather<double, dpt4><<<nb, 256, 0, s>>>((const double*)pos, (const double*)mass, perm, N, (dpt4*)spos, inv);
+    return 1;
 }
 
 // ---------------------------------------------------------------- tree
@@ -340,7 +345,7 @@ void tree_layout(int64_t N, Tree& t) {
     t.off[0] = off;  // total node count
 }
 
-void launch_tree(const void* spos, int dtype, int64_t N, Tree& t, cudaStream_t s) {
+int launch_tree(const void* spos, int dtype, int64_t N, Tree& t, cudaStream_t s) {
     int64_t nb = t.count[1];
     unsigned g = (unsigned)((nb * 32 + 255) / 256);
     if (dtype == VT_F32)
@@ -353,6 +358,7 @@ void launch_tree(const void* spos, int dtype, int64_t N, Tree& t, cudaStream_t s
         k_tree_level<<<gg, 256, 0, s>>>(t.lo + t.off[l - 1], t.hi + t.off[l - 1], t.count[l - 1], t.lo + t.off[l],
                                         t.hi + t.off[l], nn);
     }
+    return t.levels;
 }
 
 }  // namespace vt

@@ -18,14 +18,14 @@ def lib():
 def test_exports_every_declared_symbol(lib):
     names = binding.header_symbols()
     assert {"vt_build", "vt_cells", "vt_density", "vt_gradient", "vt_grid_density", "vt_backward", "vt_status",
-            "vt_destroy", "vt_error_string", "vt_default_params"} <= set(names)
+            "vt_destroy", "vt_error_string", "vt_default_params", "vt_last_error_detail"} <= set(names)
     for n in names:
         assert hasattr(lib, n), n
 
 
 def test_default_params_and_error_strings(lib):
     p = binding.vt_default_params()
-    assert p.precision == binding.VT_FILTER32 and p.k_target == 40 and p.max_passes == 24 and p.face_pool == 24
+    assert p.precision == binding.VT_FILTER32 and p.k_target == 40 and p.max_passes == 1000 and p.face_pool == 24
     assert lib.vt_default_params(None) == binding.VT_ERR_INVALID
     for code in range(0, -9, -1):
         assert binding.error_string(code) != "unknown error code"
