@@ -161,6 +161,28 @@ int vt_grid_density(vt_handle h, int G, int S, void *grid);
  */
 int vt_backward(vt_handle h, const void *dL_dV, double dL_dE, void *dL_dpos);
 
+/*
+ * vt_volumes_noalloc -- cell volumes of a small periodic or bounded point set without any device
+ * allocation.  The paper has no counterpart: this is for callers that cannot call cudaMalloc (inside
+ * another library's memory pool, on hosts that forbid allocation after start-up, or where an allocation
+ * would synchronise the device).  It runs the same kernels as vt_build + vt_cells with FP32-filtered
+ * clipping, and all of its scratch memory lives in one file-scope device array of about 8 MB that every
+ * GPU using the library holds until the process exits.
+ *   pos      device [N][3] (dtype VT_F32 or VT_F64), same rules as vt_build
+ *   N        1 <= N <= VT_NOALLOC_MAX_N; larger sets return VT_ERR_CAPACITY
+ *   box_lo, box_hi, periodic: as vt_build (periodic boxes need lengths representable in FP32)
+ *   vol      device [N] output, dtype of pos
+ *   stream   cudaStream_t; the call synchronises it once (to read the status words)
+ * All calls share the array and it keeps the last call's contents; calls whose work overlaps on the GPU
+ * (other streams or host threads) race and must be serialised by the caller.  The first call on a device
+ * looks up the array's device address with that device current: make that first call before any stream
+ * capture.  It calls no cudaMalloc, cudaFree or allocating library routine.  Errors as vt_build, plus
+ * VT_ERR_CAPACITY when the set is too large or its facets do not fit the fixed pool.
+ */
+#define VT_NOALLOC_MAX_N 8192
+int vt_volumes_noalloc(const void *pos, int dtype, int64_t N, const double box_lo[3], const double box_hi[3],
+                       int periodic, void *vol, void *stream);
+
 /* vt_status -- counters and the sticky device error; synchronises the stream. */
 int vt_status(vt_handle h, vt_stats *out);
 

@@ -93,6 +93,9 @@ def load_library(path: str = LIB_PATH):
     lib.vt_backward.restype = i32
     lib.vt_status.argtypes = [P, ctypes.POINTER(vt_stats)]
     lib.vt_status.restype = i32
+    lib.vt_volumes_noalloc.argtypes = [P, i32, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       i32, P, P]
+    lib.vt_volumes_noalloc.restype = i32
     lib.vt_last_error_detail.argtypes = [ctypes.POINTER(ctypes.c_int)]
     lib.vt_last_error_detail.restype = i32
     lib.vt_error_string.argtypes = [i32]
@@ -232,6 +235,21 @@ def vt_destroy(h: Handle) -> None:
     if h is not None and h.ptr is not None and h.ptr.value:
         load_library().vt_destroy(h.ptr)
         h.ptr = None
+
+
+VT_NOALLOC_MAX_N = 8192
+
+
+def vt_volumes_noalloc(pos, box_lo, box_hi, periodic, vol, stream=None) -> None:
+    """Cell volumes of at most VT_NOALLOC_MAX_N particles into ``vol`` without any device allocation
+    (for callers that cannot allocate); ``pos`` and ``vol`` are CUDA tensors the caller owns."""
+    import torch
+
+    lo = (ctypes.c_double * 3)(*[float(v) for v in (box_lo if hasattr(box_lo, "__len__") else (box_lo,) * 3)])
+    hi = (ctypes.c_double * 3)(*[float(v) for v in (box_hi if hasattr(box_hi, "__len__") else (box_hi,) * 3)])
+    dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
+    _check(load_library().vt_volumes_noalloc(_ptr(pos), dt, pos.shape[0], lo, hi, int(bool(periodic)), _ptr(vol),
+                                             _stream_ptr(stream)), "vt_volumes_noalloc")
 
 
 # ---------------------------------------------------------------- convenience wrappers
