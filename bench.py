@@ -46,6 +46,7 @@ UNIT = "cells/s"
 WORK = {
     "clustered16M": {"n_cert": 163.2, "verts": 26.74, "faces": 15.37},
     "clustered2M": {"n_cert": 150.0, "verts": 26.7, "faces": 15.3},
+    "clustered64k": {"n_cert": 175.8, "verts": 26.4, "faces": 15.2},
     "uniform4096": {"n_cert": 42.4, "verts": 27.1, "faces": 15.56},
 }
 FP32_LANES_PER_SM = 128
@@ -69,6 +70,11 @@ def workload(name):
         L = 100.0
         gen = lambda: inputs.clustered(2097152, L=L, seed=1)  # noqa: E731
         desc = dict(workload="clustered 2,097,152 FP32 points, periodic box L=100, seed 1", N=2097152, L=L, grid=256)
+    elif name == "clustered64k":
+        L = float(np.float32(100.0 * (65536 / 2097152) ** (1.0 / 3.0)))
+        gen = lambda: inputs.clustered(65536, L=L, seed=1)  # noqa: E731
+        desc = dict(workload="clustered 65,536 FP32 points (the 2M recipe scaled), periodic box L=%.4f, seed 1" % L,
+                    N=65536, L=L, grid=64)
     elif name == "uniform4096":
         L = 1.0
         gen = lambda: inputs.uniform(4096, seed=0, dtype=np.float32)  # noqa: E731
@@ -365,7 +371,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="clustered16M")
     ap.add_argument("--precision", choices=["filter32", "plain64"], default="filter32")
-    ap.add_argument("--cpu-sample", type=int, default=8192)
+    ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

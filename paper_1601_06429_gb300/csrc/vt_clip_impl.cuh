@@ -107,7 +107,8 @@ __device__ __forceinline__ T warp_max(T v) {
     for (int o = 16; o; o >>= 1) { T w = __shfl_xor_sync(0xffffffffu, v, o); v = v > w ? v : w; }
     return v;
 }
-__device__ __forceinline__ double warp_sum_d(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -172,6 +173,12 @@ __device__ __forceinline__ double dcomp_shift_d(double xj, double xi, double L, 
 template <typename CT> __device__ __forceinline__ CT f_fma(CT a, CT b, CT c);
 template <> __device__ __forceinline__ float f_fma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 template <> __device__ __forceinline__ double f_fma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// x - e rounded down and x + e rounded up, as floats
+__device__ __forceinline__ float sub_dn(float x, float e) { return __fsub_rd(x, e); }
+__device__ __forceinline__ float add_up(float x, float e) { return __fadd_ru(x, e); }
+__device__ __forceinline__ float sub_dn(double x, double e) { return __double2float_rd(x - e); }
+__device__ __forceinline__ float add_up(double x, double e) { return __double2float_ru(x + e); }
 
 // bit pattern of a non-negative value (order preserving), and back
 template <typename CT> __device__ __forceinline__ unsigned long long fbits(CT v);
@@ -736,12 +743,12 @@ __device__ __forceinline__ void cell_box(const WarpSmem<CT, TP>& S, const CellSt
             int s = e * 32 + lane;
             CT ev = S.tev[s];
             if (!(ev < (CT)INFINITY)) inf = true;
-            lo0 = fminf(lo0, __double2float_rd((double)(S.tx[s] - ev)));
-            lo1 = fminf(lo1, __double2float_rd((double)(S.ty[s] - ev)));
-            lo2 = fminf(lo2, __double2float_rd((double)(S.tz[s] - ev)));
-            hi0 = fmaxf(hi0, __double2float_ru((double)(S.tx[s] + ev)));
-            hi1 = fmaxf(hi1, __double2float_ru((double)(S.ty[s] + ev)));
-            hi2 = fmaxf(hi2, __double2float_ru((double)(S.tz[s] + ev)));
+            lo0 = fminf(lo0, sub_dn(S.tx[s], ev));
+            lo1 = fminf(lo1, sub_dn(S.ty[s], ev));
+            lo2 = fminf(lo2, sub_dn(S.tz[s], ev));
+            hi0 = fmaxf(hi0, add_up(S.tx[s], ev));
+            hi1 = fmaxf(hi1, add_up(S.ty[s], ev));
+            hi2 = fmaxf(hi2, add_up(S.tz[s], ev));
         }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -818,11 +825,12 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
     // bins over the bit patterns of the non-negative |d|^2 (monotone), so narrowing never underflows
     const unsigned long long blo = fbits<CT>(rlo2), bhi = fbits<CT>(rhi2);
     const unsigned long long bwidth = bhi > blo ? bhi - blo : 1ull;
+    const float binsc = (float)HIST_BINS / (float)bwidth;
     // conservative float radius for box pruning
-    float rad = (float)sqrt((double)rhi2) * 1.0001f + 1e-30f;
+    float rad = sqrtf((float)rhi2) * 1.0001f + 1e-30f;
     float rad2 = rad * rad;
     // nodes entirely within the inner radius hold only examined points
-    float inner2 = (float)((double)rlo2 * 0.9999);
+    float inner2 = (float)rlo2 * 0.9999f;
     // rounding tolerance of the support test: relative 1e-5 of its terms
     const float bext = fmaxf(fmaxf(fmaxf(-bmin[0], bmax[0]), fmaxf(-bmin[1], bmax[1])), fmaxf(-bmin[2], bmax[2]));
     const float stol = 1e-5f * (4.f * bext * rad + rad2) + 1e-30f;
@@ -892,11 +900,11 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
             }
             if (hit) {
                 unsigned long long bb = fbits<CT>(d2);
-                int b = bb <= blo ? 0 : (int)min((unsigned long long)(HIST_BINS - 1),
-                                                 (unsigned long long)((double)(bb - blo) * HIST_BINS / (double)bwidth));
+                int b = bb <= blo ? 0 : min(HIST_BINS - 1, (int)((float)(bb - blo) * binsc));
                 atomicAdd(&S.hist[b], 1u);
             }
             count += __popc(m);
+            if (count > 4 * Cap<TP>::CAND) return -3;  // far too many: the caller shrinks the radius
         } else {
             int cl = lvl - 1;
             int64_t c = node * 32 + lane;
@@ -970,7 +978,7 @@ __device__ __forceinline__ uint32_t succ_tri(const WarpSmem<CT, TP>& S, uint32_t
 
 // Test the lanes' planes against the vertex slots in masks[] and OR the beyond-the-plane slots into outm[].
 template <typename P, typename CT, bool EXACT, int TP>
-__device__ __forceinline__ void test_slots(const WarpSmem<CT, TP>& S, const unsigned* masks, bool act, CT nx, CT ny, CT nz,
+__device__ __noinline__ void test_slots(const WarpSmem<CT, TP>& S, const unsigned* masks, bool act, CT nx, CT ny, CT nz,
                                            CT h, CT nrm, CT hb, uint32_t src, int code, unsigned* outm,
                                            const P* spos, const Geometry& g, uint32_t self, double* xws,
                                            CellCounters& cc, bool& need_exact, bool& ovf) {
@@ -1113,6 +1121,14 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             cc.n_collect++;
             if (cnt > 0) cc.n_collected += cnt;
             if (cnt == -2) return CAP_STACK;
+            if (cnt == -3) {  // aborted: halve the radius step and retry
+                CT r = sqrt(rhi2), rl = sqrt(rlo2);
+                CT rn = rl + (CT)0.5 * (r - rl);
+                CT rn2 = rn * rn;
+                rhi2 = rn2 > rlo2 ? rn2 : fromfbits<CT>(fbits<CT>(rlo2) + 1);
+                cnt = -1;
+                continue;
+            }
             if (cnt <= K::CAND) break;
             // too many: keep the largest prefix of histogram bins that fits (at least the first bin, narrowed
             // again if needed)
@@ -1124,7 +1140,9 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
                 keep = b + 1;
             }
             unsigned long long blo = fbits<CT>(rlo2), bhi = fbits<CT>(rhi2);
-            unsigned long long nb = blo + (unsigned long long)((double)(bhi - blo) * (keep > 0 ? keep : 1) / HIST_BINS);
+            // exact integer split of the bit-pattern range (a bin that the float binning put a point in may
+            // shift by one; the loop only needs the count to drop)
+            unsigned long long nb = blo + (bhi - blo) / HIST_BINS * (unsigned long long)(keep > 0 ? keep : 1);
             if (nb <= blo) nb = blo + 1;
             if (nb >= bhi) return CAP_CAND;
             rhi2 = fromfbits<CT>(nb);
@@ -1230,16 +1248,17 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         // that the density seen so far says holds about 3/4 of a pass's capacity)
         {
             CT nxt = (CT)4 * R2 * ((CT)1 + (CT)32 * u);
-            double rh = sqrt((double)rhi2), rl = sqrt((double)rlo2);
-            double shell = rh * rh * rh - rl * rl * rl;
-            double lim = 4.0 * (double)rhi2;
-            if (A.radius_policy == 1 && cnt > 0 && shell > 0.0) {
-                double r3 = rh * rh * rh + 0.75 * K::CAND * shell / (double)cnt;
-                double r = cbrt(r3);
-                lim = fmin(lim, fmax(r * r, 1.21 * (double)rhi2));
+            float lim = 4.f * (float)rhi2;
+            if (A.radius_policy == 1 && cnt > 0) {
+                float rh = sqrtf((float)rhi2), rl = sqrtf((float)rlo2);
+                float shell = rh * rh * rh - rl * rl * rl;
+                if (shell > 0.f) {
+                    float r = cbrtf(rh * rh * rh + 0.75f * K::CAND * shell / (float)cnt);
+                    lim = fminf(lim, fmaxf(r * r, 1.21f * (float)rhi2));
+                }
             }
             rlo2 = rhi2;
-            rhi2 = (double)nxt < lim ? nxt : (CT)lim;
+            rhi2 = nxt < (CT)lim ? nxt : (CT)lim;
         }
     }
     if (!done) return (!EXACT && !(R2 < (CT)INFINITY)) ? RC_NEED_EXACT : VT_ERR_SECURITY;
@@ -1269,10 +1288,10 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
     }
     // facets: lane (chunk c) walks plane c*32+lane; fan from the facet's first vertex
     constexpr int PCH = K::MAXP / 32;
-    double vol = 0.0, mzx = 0.0, mzy = 0.0, mzz = 0.0, m2 = 0.0;
+    CT vol = 0, mzx = 0, mzy = 0, mzz = 0, m2 = 0;
     CT fA[PCH], fcx[PCH], fcy[PCH], fcz[PCH];
     bool fem[PCH];
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < PCH; c++) {
         fem[c] = false;
         fA[c] = fcx[c] = fcy[c] = fcz[c] = (CT)0;
@@ -1311,19 +1330,19 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         // distance from the site to the facet plane; tetrahedra (site, fan triangle) give
         // V_f = dist A_f / 3, first moment dist * sum(at (v0+v1+v2)/3) / 4, second moment dist/30 * sum(at s2)
         CT dist = S.ph[p] * inrm;
-        vol += (double)(dist * A_) * (1.0 / 3.0);
-        mzx += (double)(dist * csx) * 0.25;
-        mzy += (double)(dist * csy) * 0.25;
-        mzz += (double)(dist * csz) * 0.25;
-        m2 += (double)(dist * sm2) * (1.0 / 30.0);
+        vol += dist * A_ * (CT)(1.0 / 3.0);
+        mzx += dist * csx * (CT)0.25;
+        mzy += dist * csy * (CT)0.25;
+        mzz += dist * csz * (CT)0.25;
+        m2 += dist * sm2 * (CT)(1.0 / 30.0);
         if (A_ != (CT)0) { fcx[c] = csx / A_; fcy[c] = csy / A_; fcz[c] = csz / A_; }
         fA[c] = A_;
         fem[c] = (p >= 6) && S.pcode[p] < 27;
     }
-    vol = warp_sum_d(vol);
-    m2 = warp_sum_d(m2);
-    mzx = warp_sum_d(mzx); mzy = warp_sum_d(mzy); mzz = warp_sum_d(mzz);
-    const double sg = vol < 0 ? -1.0 : 1.0;
+    vol = warp_sum<CT>(vol);
+    m2 = warp_sum<CT>(m2);
+    mzx = warp_sum<CT>(mzx); mzy = warp_sum<CT>(mzy); mzz = warp_sum<CT>(mzz);
+    const CT sg = vol < 0 ? (CT)-1 : (CT)1;
     vol *= sg; m2 *= sg;
     int nf_total = 0;
 #pragma unroll
@@ -1345,7 +1364,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
                 int p = c * 32 + (int)lane;
                 Face f;
                 f.dx = (float)S.pnx[p]; f.dy = (float)S.pny[p]; f.dz = (float)S.pnz[p];
-                f.area = (float)(sg * (double)fA[c]);
+                f.area = (float)(sg * fA[c]);
                 f.cx = (float)fcx[c]; f.cy = (float)fcy[c]; f.cz = (float)fcz[c];
                 f.nbr = S.psrc[p];
                 A.faces[start + acc + __popc(m & lt)] = f;
@@ -1355,10 +1374,10 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
     }
     if (lane == 0) {
         CellOut co;
-        co.vol = vol;
-        co.zx = (float)(vol > 0 ? sg * mzx / vol : 0.0);
-        co.zy = (float)(vol > 0 ? sg * mzy / vol : 0.0);
-        co.zz = (float)(vol > 0 ? sg * mzz / vol : 0.0);
+        co.vol = (double)vol;
+        co.zx = (float)(vol > 0 ? sg * mzx / vol : (CT)0);
+        co.zy = (float)(vol > 0 ? sg * mzy / vol : (CT)0);
+        co.zz = (float)(vol > 0 ? sg * mzz / vol : (CT)0);
         co.mom2 = (float)m2;
         A.cell[self] = co;
         A.face_start[self] = start;
