@@ -220,3 +220,11 @@ def test_clustered_2M_sampled(oracle_mod):
     x = inputs.clustered(2097152, L=100.0, seed=1)
     g = _sampled(x, 100.0, "filter32", 2e-5, oracle_mod, 4096, 2)
     assert g["stats"]["device_error"] == 0
+
+
+def test_clustered_16M_sampled(oracle_mod):
+    # the benchmark workload at full size, FP32 filter: sampled cells against the oracle (which builds its
+    # k-d tree over all 16.7 M points), total volume and neighbour symmetry over every particle
+    x = inputs.clustered(16777216, L=200.0, seed=2)
+    g = _sampled(x, 200.0, "filter32", 2e-5, oracle_mod, 2048, 7)
+    assert g["stats"]["device_error"] == 0
