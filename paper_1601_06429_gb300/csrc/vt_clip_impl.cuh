@@ -323,10 +323,13 @@ __device__ __forceinline__ int x_sign(const Xe& e) {
     return (t > 0) - (t < 0);
 }
 
+// A plane's source: code 0..26 = bisector with particle src under image shift `code`; 27..32 = box wall
+// (27 + w); 33..38 = artificial wall 33 + w at distance B from the site, with B's float bits in src.
 struct PRef {
     uint32_t src;
     int code;
 };
+constexpr int CODE_WALL = 27, CODE_ART = 33;
 
 // exact row (n_x, n_y, n_z, w) of a plane, positively scaled: bisector -> (2d, |d|^2), wall -> (n, h)
 template <typename P>
@@ -350,14 +353,15 @@ __device__ void x_row(XWork& w, Xe row[4], const P* spos, const Geometry& g, uin
             x_mul_into(w, row[3], d[c], d[c], false);
         }
     } else {
-        int wall = r.code - 27, axis = wall >> 1;
+        int wall = r.code - (r.code >= CODE_ART ? CODE_ART : CODE_WALL), axis = wall >> 1;
         bool upper = (wall & 1) == 0;
         for (int c = 0; c < 3; c++) {
             row[c] = x_alloc(w, 1);
             if (c == axis) x_grow(w, row[c], upper ? 1.0 : -1.0);
         }
         row[3] = x_alloc(w, 3);
-        if (upper) { x_grow(w, row[3], g.hi[axis]); x_grow(w, row[3], -xi[axis]); }
+        if (r.code >= CODE_ART) x_grow(w, row[3], (double)__uint_as_float(r.src));
+        else if (upper) { x_grow(w, row[3], g.hi[axis]); x_grow(w, row[3], -xi[axis]); }
         else { x_grow(w, row[3], xi[axis]); x_grow(w, row[3], -g.lo[axis]); }
     }
 }
@@ -428,13 +432,14 @@ __device__ void plane64(const P* spos, const Geometry& g, uint32_t self, PRef r,
         h = 0.5 * __fma_rn(nz, nz, __fma_rn(ny, ny, nx * nx));
         nrm = sqrt(2.0 * h);
     } else {
-        int wall = r.code - 27, axis = wall >> 1;
+        int wall = r.code - (r.code >= CODE_ART ? CODE_ART : CODE_WALL), axis = wall >> 1;
         bool upper = (wall & 1) == 0;
         double xi = axis == 0 ? (double)pi.x : axis == 1 ? (double)pi.y : (double)pi.z;
         nx = ny = nz = 0.0;
         double sgn = upper ? 1.0 : -1.0;
         if (axis == 0) nx = sgn; else if (axis == 1) ny = sgn; else nz = sgn;
-        h = upper ? __dsub_rn(g.hi[axis], xi) : __dsub_rn(xi, g.lo[axis]);
+        if (r.code >= CODE_ART) h = (double)__uint_as_float(r.src);
+        else h = upper ? __dsub_rn(g.hi[axis], xi) : __dsub_rn(xi, g.lo[axis]);
         nrm = 1.0;
     }
 }
@@ -602,7 +607,7 @@ __device__ int resolve(const WarpSmem<CT, TP>& S, int s, bool need, uint32_t src
         sd = side64<P>(spos, g, self, ra, rb, rc, rj);
         cc.n_fp64++;
 #ifdef VT_PHASE_TIMERS
-        if (!(S.tev[s] < (CT)INFINITY)) cc.t[9]++;
+        if (a < 6 || b < 6 || c < 6) cc.t[9]++;  // undecided test on a vertex that still touches the initial cube
 #endif
     }
     bool pending = need && sd == 0;
@@ -968,6 +973,7 @@ __device__ void sort_cand(WarpSmem<CT, TP>& S, int n) {
 // ------------------------------------------------------------------ the cell
 constexpr int RC_NEED_EXACT = 1000;
 constexpr int RC_POOL = 1001;
+constexpr int RC_RETRY_BOX = 1002;
 
 // successor of triangle t around plane p: the neighbour across the edge (corner before p) -> p
 template <typename CT, int TP>
@@ -1001,7 +1007,8 @@ __device__ __noinline__ void test_slots(const WarpSmem<CT, TP>& S, const unsigne
 }
 
 template <typename P, typename CT, bool EXACT, int TP>
-__device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, double* xws, CellCounters& cc) {
+__device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, double* xws, CellCounters& cc,
+                       bool small_box) {
     const P* spos = (const P*)A.spos;
     const Geometry& g = A.geo;
     const unsigned lane = lane_id(), lt = lanemask_lt();
@@ -1012,64 +1019,6 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
 #pragma unroll
     for (int e = 0; e < TP; e++) C.vm[e] = 0u;
     C.np = 6;
-    // initial planes: periodic self-images (+x,-x,+y,-y,+z,-z) or box walls
-    if (lane < 6) {
-        int axis = lane >> 1;
-        bool upper = (lane & 1) == 0;
-        CT nx = 0, ny = 0, nz = 0, h, nrm;
-        int code;
-        if (g.periodic) {
-            CT Lc = (CT)g.L[axis];
-            CT sg = upper ? Lc : -Lc;
-            if (axis == 0) nx = sg; else if (axis == 1) ny = sg; else nz = sg;
-            h = (CT)(0.5 * g.L[axis] * g.L[axis]);
-            nrm = Lc;
-            int sh[3] = {0, 0, 0};
-            sh[axis] = upper ? 1 : -1;
-            code = code_of(sh[0], sh[1], sh[2]);
-        } else {
-            CT sg = upper ? (CT)1 : (CT)-1;
-            if (axis == 0) nx = sg; else if (axis == 1) ny = sg; else nz = sg;
-            double xi = axis == 0 ? (double)pi.x : axis == 1 ? (double)pi.y : (double)pi.z;
-            h = (CT)(upper ? (g.hi[axis] - xi) : (xi - g.lo[axis]));
-            nrm = (CT)1;
-            code = 27 + (int)lane;
-        }
-        S.pnx[lane] = nx; S.pny[lane] = ny; S.pnz[lane] = nz; S.ph[lane] = h; S.pnrm[lane] = nrm;
-        S.psrc[lane] = self; S.pcode[lane] = (uint8_t)code;
-    }
-    __syncwarp();
-    // 8 corners: planes x upper 0 / lower 1, y 2/3, z 4/5; (X,Y,Z) if the sign product is positive, else
-    // (X,Z,Y): every triangle then lists its planes counter-clockwise seen from outside
-    if (lane < 8) {
-        int sx = (lane & 1) ? -1 : 1, sy = (lane & 2) ? -1 : 1, sz = (lane & 4) ? -1 : 1;
-        uint32_t X = (lane & 1) ? 1 : 0, Y = (lane & 2) ? 3 : 2, Z = (lane & 4) ? 5 : 4;
-        S.tid[lane] = (sx * sy * sz > 0) ? pack<TP>(X, Y, Z) : pack<TP>(X, Z, Y);
-        tri_vertex<CT, TP>(S, lane);
-    }
-    __syncwarp();
-    if (lane < 8) {  // adjacency of the initial octahedron by search
-        uint32_t ids[3];
-        unpack<TP>(S.tid[lane], ids[0], ids[1], ids[2]);
-        uint32_t nb[3] = {0u, 0u, 0u};
-        for (int k = 0; k < 3; k++) {
-            uint32_t x = ids[k], y = ids[(k + 1) % 3];
-            for (int t2 = 0; t2 < 8; t2++) {
-                uint32_t o[3];
-                unpack<TP>(S.tid[t2], o[0], o[1], o[2]);
-                for (int q = 0; q < 3; q++)
-                    if (o[q] == y && o[(q + 1) % 3] == x) nb[k] = (uint32_t)t2;
-            }
-        }
-        S.tadj[lane] = adj_pack(nb[0], nb[1], nb[2]);
-    }
-    C.vm[0] = 0xFFu;
-    C.hw = 8;
-    __syncwarp();
-    CT R2 = rmax2<CT, TP>(S, C);
-    float bmin[3], bmax[3];
-    cell_box<CT, TP>(S, C, bmin, bmax);
-
     // first radius from the bucket mates: 1.6 x the distance of the ~11th nearest
     CT rhi2;
     {
@@ -1105,6 +1054,79 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         }
         rhi2 = (CT)dk * (CT)2.6;
     }
+    // Initial polytope.  With small_box the cell starts as a cube of half-side B = 3 r (r the first search
+    // radius) made of artificial walls: a polytope on the scale of the cell keeps the vertex error bounds
+    // small (the box of the periodic self-images has vertices at L/2).  If the final cell still touches an
+    // artificial wall the box was too small and the caller redoes the cell without it.  Otherwise the
+    // periodic self-images (x_i +- L e_k) or the box walls bound the cell.
+    const double lminb = fmin(g.L[0], fmin(g.L[1], g.L[2]));
+    const float Bf = small_box ? (float)(3.0 * sqrt((double)rhi2)) : 0.f;
+    if (lane < 6) {
+        int axis = lane >> 1;
+        bool upper = (lane & 1) == 0;
+        CT nx = 0, ny = 0, nz = 0, h, nrm;
+        int code;
+        uint32_t src = self;
+        double xi = axis == 0 ? (double)pi.x : axis == 1 ? (double)pi.y : (double)pi.z;
+        double real = g.periodic ? 0.5 * g.L[axis] : (upper ? g.hi[axis] - xi : xi - g.lo[axis]);
+        if (small_box && (double)Bf < (g.periodic ? 0.49 * lminb : real)) {
+            CT sg = upper ? (CT)1 : (CT)-1;
+            if (axis == 0) nx = sg; else if (axis == 1) ny = sg; else nz = sg;
+            h = (CT)Bf;
+            nrm = (CT)1;
+            code = CODE_ART + (int)lane;
+            src = __float_as_uint(Bf);
+        } else if (g.periodic) {
+            CT Lc = (CT)g.L[axis];
+            CT sg = upper ? Lc : -Lc;
+            if (axis == 0) nx = sg; else if (axis == 1) ny = sg; else nz = sg;
+            h = (CT)(0.5 * g.L[axis] * g.L[axis]);
+            nrm = Lc;
+            int sh[3] = {0, 0, 0};
+            sh[axis] = upper ? 1 : -1;
+            code = code_of(sh[0], sh[1], sh[2]);
+        } else {
+            CT sg = upper ? (CT)1 : (CT)-1;
+            if (axis == 0) nx = sg; else if (axis == 1) ny = sg; else nz = sg;
+            h = (CT)real;
+            nrm = (CT)1;
+            code = CODE_WALL + (int)lane;
+        }
+        S.pnx[lane] = nx; S.pny[lane] = ny; S.pnz[lane] = nz; S.ph[lane] = h; S.pnrm[lane] = nrm;
+        S.psrc[lane] = src; S.pcode[lane] = (uint8_t)code;
+    }
+    __syncwarp();
+    // 8 corners: planes x upper 0 / lower 1, y 2/3, z 4/5; (X,Y,Z) if the sign product is positive, else
+    // (X,Z,Y): every triangle then lists its planes counter-clockwise seen from outside
+    if (lane < 8) {
+        int sx = (lane & 1) ? -1 : 1, sy = (lane & 2) ? -1 : 1, sz = (lane & 4) ? -1 : 1;
+        uint32_t X = (lane & 1) ? 1 : 0, Y = (lane & 2) ? 3 : 2, Z = (lane & 4) ? 5 : 4;
+        S.tid[lane] = (sx * sy * sz > 0) ? pack<TP>(X, Y, Z) : pack<TP>(X, Z, Y);
+        tri_vertex<CT, TP>(S, lane);
+    }
+    __syncwarp();
+    if (lane < 8) {  // adjacency of the initial octahedron by search
+        uint32_t ids[3];
+        unpack<TP>(S.tid[lane], ids[0], ids[1], ids[2]);
+        uint32_t nb[3] = {0u, 0u, 0u};
+        for (int k = 0; k < 3; k++) {
+            uint32_t x = ids[k], y = ids[(k + 1) % 3];
+            for (int t2 = 0; t2 < 8; t2++) {
+                uint32_t o[3];
+                unpack<TP>(S.tid[t2], o[0], o[1], o[2]);
+                for (int q = 0; q < 3; q++)
+                    if (o[q] == y && o[(q + 1) % 3] == x) nb[k] = (uint32_t)t2;
+            }
+        }
+        S.tadj[lane] = adj_pack(nb[0], nb[1], nb[2]);
+    }
+    C.vm[0] = 0xFFu;
+    C.hw = 8;
+    __syncwarp();
+    CT R2 = rmax2<CT, TP>(S, C);
+    float bmin[3], bmax[3];
+    cell_box<CT, TP>(S, C, bmin, bmax);
+
     CT rlo2 = 0;
     const double lmin = fmin(g.L[0], fmin(g.L[1], g.L[2]));
     CT cap2 = g.periodic ? (CT)(0.249 * lmin * lmin)
@@ -1281,10 +1303,13 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         }
     }
     __syncwarp();
-    // a facet on an initial plane: box wall (bounded) is fine; own periodic image is not supported
-    if (g.periodic) {
-        bool bad = (lane < 6) && S.u.em.first[lane] != 0xffffffffu;
-        if (__any_sync(0xffffffffu, bad)) return VT_ERR_UNSUPPORTED;
+    // a facet on an initial plane: an artificial wall means the start box was too small (redo without it);
+    // a box wall (bounded) is fine; an own periodic image is not supported
+    {
+        bool on = (lane < 6) && S.u.em.first[lane] != 0xffffffffu;
+        bool art = on && S.pcode[lane] >= CODE_ART;
+        if (__any_sync(0xffffffffu, art)) return RC_RETRY_BOX;
+        if (g.periodic && __any_sync(0xffffffffu, on)) return VT_ERR_UNSUPPORTED;
     }
     // facets: lane (chunk c) walks plane c*32+lane; fan from the facet's first vertex
     constexpr int PCH = K::MAXP / 32;
@@ -1412,7 +1437,8 @@ __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
         for (uint32_t q = base; q < base + chunk && q < lim; q++) {
             uint32_t self = EXACT ? A.exact_list[q] : q;
             VT_T0(tall);
-            int rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc);
+            int rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, !EXACT);
+            if (rc == RC_RETRY_BOX) rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, false);
             VT_T1(cc, 5, tall);
             __syncwarp();
             if (!EXACT && rc <= -100) rc = RC_NEED_EXACT;  // capacity: the larger exact kernel takes the cell
