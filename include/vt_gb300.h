@@ -151,6 +151,15 @@ int vt_gradient(vt_handle h, void *grad);
 int vt_grid_density(vt_handle h, int G, int S, void *grid);
 
 /*
+ * vt_moments -- first and second moments of every cell (no counterpart in the paper; they define the
+ * centroidal Voronoi energy used with vt_backward).
+ *   centroid  device [N][3] or NULL: the cell's centroid, in the frame of the positions (wrapped into
+ *             [box_lo, box_hi) for periodic boxes)
+ *   energy    device [N] or NULL: E_i = integral over cell i of |y - x_i|^2
+ */
+int vt_moments(vt_handle h, void *centroid, void *energy);
+
+/*
  * vt_backward -- adjoint of the cell volumes (no counterpart in the paper).
  * For a loss L with dL/dV_i = dL_dV[i] and, optionally, a uniform weight
  * dL_dE on the centroidal (CVT) energy E = sum_i integral_{cell i} |y - x_i|^2:

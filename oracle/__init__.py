@@ -261,19 +261,18 @@ def volume_adjoint(res, pos, box_lo=0.0, box_hi=1.0, g_vol=None, g_energy=None):
     off = res["face_off"]
     if g_vol is not None:
         gV = np.asarray(g_vol, dtype=np.float64)
-        for k in range(len(off) - 1):
-            i = wh[k]
-            for f in range(off[k], off[k + 1]):
-                j = res["f_nbr"][f]
-                if j < 0 or j == i:
-                    continue
-                xj = pos[j] + res["f_shift"][f] * L
-                r = np.linalg.norm(xj - pos[i])
-                A = res["f_area"][f]
-                c = res["f_cen"][f]
-                out[i] += gV[i] * A * (c - pos[i]) / r
-                out[j] += gV[i] * A * (xj - c) / r
+        i = np.repeat(wh, np.diff(off))            # cell of each facet
+        j = res["f_nbr"]
+        keep = (j >= 0) & (j != i)                 # walls and own images do not move
+        i, j = i[keep], j[keep]
+        xj = pos[j] + res["f_shift"][keep] * L     # the image that shares the facet
+        r = np.linalg.norm(xj - pos[i], axis=1)
+        A = res["f_area"][keep]
+        c = res["f_cen"][keep]
+        w = (gV[i] * A / r)[:, None]
+        np.add.at(out, i, w * (c - pos[i]))        # dV_i/dx_i term
+        np.add.at(out, j, w * (xj - c))            # dV_i/dx_j term
     if g_energy is not None:
         ge = float(g_energy)
-        out += ge * 2.0 * res["vol"][:, None] * (pos[wh] - res["cen"])
+        out[wh] += ge * 2.0 * res["vol"][:, None] * (pos[wh] - res["cen"])
     return out

@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_gradient.restype = i32
     lib.vt_grid_density.argtypes = [P, i32, i32, P]
     lib.vt_grid_density.restype = i32
+    lib.vt_moments.argtypes = [P, P, P]
+    lib.vt_moments.restype = i32
     lib.vt_backward.argtypes = [P, P, ctypes.c_double, P]
     lib.vt_backward.restype = i32
     lib.vt_status.argtypes = [P, ctypes.POINTER(vt_stats)]
@@ -219,6 +221,10 @@ def vt_grid_density(h: Handle, G: int, S: int, grid) -> None:
     _check(load_library().vt_grid_density(h.ptr, int(G), int(S), _ptr(grid)), "vt_grid_density")
 
 
+def vt_moments(h: Handle, centroid=None, energy=None) -> None:
+    _check(load_library().vt_moments(h.ptr, _ptr(centroid), _ptr(energy)), "vt_moments")
+
+
 def vt_backward(h: Handle, dL_dV, dL_dE: float, dL_dpos) -> None:
     _check(load_library().vt_backward(h.ptr, _ptr(dL_dV), float(dL_dE), _ptr(dL_dpos)), "vt_backward")
 
@@ -287,6 +293,16 @@ def grid_density(h: Handle, G: int, S: int = 1):
     g = torch.empty(G, G, G, dtype=h.dtype, device=h.device)
     vt_grid_density(h, G, S, g)
     return g
+
+
+def moments(h: Handle):
+    """(centroid [N,3], energy [N]) as new CUDA tensors."""
+    import torch
+
+    c = torch.empty(h.N, 3, dtype=h.dtype, device=h.device)
+    e = torch.empty(h.N, dtype=h.dtype, device=h.device)
+    vt_moments(h, c, e)
+    return c, e
 
 
 def backward(h: Handle, dL_dV=None, dL_dE: float = 0.0):

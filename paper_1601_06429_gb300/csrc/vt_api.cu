@@ -309,6 +309,12 @@ int vt_grid_density(vt_handle h, int G, int S, void* grid) {
     return cuda_rc(cudaGetLastError());
 }
 
+int vt_moments(vt_handle h, void* centroid, void* energy) {
+    if (!h || (!centroid && !energy)) return VT_ERR_INVALID;
+    h->n_launches += launch_moments(h->cell, h->spos, h->dtype, h->perm, h->N, h->geo, centroid, energy, h->stream);
+    return cuda_rc(cudaGetLastError());
+}
+
 int vt_backward(vt_handle h, const void* dL_dV, double dL_dE, void* dL_dpos) {
     if (!h || !dL_dpos || !isfinite(dL_dE)) return VT_ERR_INVALID;
     h->n_launches += launch_backward(h->faces, h->face_start, h->face_count, h->cell, h->spos, h->dtype, h->perm, h->inv, h->N, dL_dV,

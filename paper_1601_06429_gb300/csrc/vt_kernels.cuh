@@ -62,6 +62,8 @@ int launch_grid(const void* spos, int dtype, int64_t N, const Geometry& g, const
                 const uint32_t* face_start, const uint16_t* face_count, const uint64_t* keys,
                 const double* dens_sorted, const uint32_t* perm, int G, int S, void* grid, DevStatus* st,
                 cudaStream_t s);
+int launch_moments(const CellOut* cell, const void* spos, int dtype, const uint32_t* perm, int64_t N,
+                   const Geometry& g, void* cen, void* energy, cudaStream_t s);
 int launch_backward(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const CellOut* cell,
                      const void* spos, int dtype, const uint32_t* perm, const uint32_t* inv, int64_t N,
                      const void* dLdV, double dLdE, void* out, cudaStream_t s);

@@ -329,6 +329,45 @@ int launch_grid(const void* spos, int dtype, int64_t N, const Geometry& g, const
     return 1;
 }
 
+// ------------------------------------------------------------------ cell moments
+// centroid z_i = x_i + (cell centroid relative to x_i), wrapped into the box when periodic, and the second
+// moment E_i = integral over the cell of |y - x_i|^2 (the centroidal Voronoi energy of the cell)
+template <typename P, typename T>
+__global__ void k_moments(const CellOut* __restrict__ cell, const P* __restrict__ spos,
+                          const uint32_t* __restrict__ perm, int64_t N, Geometry g, T* __restrict__ cen,
+                          T* __restrict__ energy) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    CellOut co = cell[k];
+    P p = spos[k];
+    uint32_t i = perm[k];
+    if (cen) {
+        double z[3] = {(double)p.x + co.zx, (double)p.y + co.zy, (double)p.z + co.zz};
+        for (int c = 0; c < 3; c++) {
+            if (g.periodic) {
+                if (z[c] >= g.hi[c]) z[c] -= g.L[c];
+                else if (z[c] < g.lo[c]) z[c] += g.L[c];
+            }
+            T v = (T)z[c];
+            if (g.periodic && v >= (T)g.hi[c]) v = (T)g.lo[c];  // a value that rounds up to hi wraps to lo
+            cen[3 * (int64_t)i + c] = v;
+        }
+    }
+    if (energy) energy[i] = (T)co.mom2;
+}
+
+int launch_moments(const CellOut* cell, const void* spos, int dtype, const uint32_t* perm, int64_t N,
+                   const Geometry& g, void* cen, void* energy, cudaStream_t s) {
+    unsigned nb = (unsigned)((N + 255) / 256);
+    if (dtype == VT_F32)
+        k_moments<float4, float><<<nb, 256, 0, s>>>(cell, (const float4*)spos, perm, N, g, (float*)cen,
+                                                     (float*)energy);
+    else
+        k_moments<dpt4, double><<<nb, 256, 0, s>>>(cell, (const dpt4*)spos, perm, N, g, (double*)cen,
+                                                    (double*)energy);
+    return 1;
+}
+
 // ------------------------------------------------------------------ backward
 // dL/dx_k = sum_j (A_kj/|r_kj|)(g_k - g_j)(c_kj - x_k) + dL_dE * 2 V_k (x_k - z_k); one thread per cell,
 // a gather over the cell's own facets (each facet is stored from both sides, so no atomics are needed).

@@ -1,0 +1,118 @@
+"""Differentiation through the Voronoi cells (torch.autograd.Function over vt_backward) and Lloyd steps.
+
+Workload: the 1,048,576-point halo (30 %) + uniform mixture in the unit periodic box, FP32, and a
+32,768-point version of the same recipe for the checks that need the oracle.
+Checks:
+  * dL/dx of L = sum_i w_i log(rho_i), w ~ U(0,1), against the oracle's analytic adjoint (all particles)
+    and against central finite differences of the oracle's FP64 volumes (h = 1e-4 scaled by the local
+    spacing, Richardson extrapolation over h and h/2) on random particles;
+  * the energy gradient 2 V (x - z) through autograd against the oracle;
+  * 50 Lloyd steps on the full set: the centroidal energy never increases; a BCC lattice is a fixed point.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1601_06429_gb300 import autograd as vta
+from paper_1601_06429_gb300 import binding as vt
+from paper_1601_06429_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1601_06429_gb300.build import build
+
+    build()
+    vt.load_library()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def mix32k(oracle_mod):
+    x = inputs.halo_uniform_mix(32768, L=1.0, seed=3)
+    o = oracle_mod.cells(x.astype(np.float64), 0.0, 1.0, True, mode="certified")
+    w = inputs.rng(4).random(len(x))
+    return x, o, w
+
+
+def _gpu_grad(x, w, precision):
+    pos = torch.from_numpy(x).cuda().requires_grad_(True)
+    vol, energy = vta.cells(pos, (0.0,) * 3, (1.0,) * 3, True, precision)
+    wt = torch.from_numpy(w).to(device=pos.device, dtype=pos.dtype)
+    loss = (wt * torch.log(1.0 / vol)).sum()  # unit masses: rho = 1 / V
+    loss.backward()
+    return pos.grad.double().cpu().numpy(), vol.double().detach().cpu().numpy()
+
+
+def test_log_density_loss_matches_oracle_adjoint(mix32k, oracle_mod):
+    x, o, w = mix32k
+    g, vol = _gpu_grad(x, w, "filter32")
+    ref = oracle_mod.volume_adjoint(o, x.astype(np.float64), g_vol=-w / o["vol"])
+    scale = np.linalg.norm(ref, axis=1)
+    err = np.linalg.norm(g - ref, axis=1)
+    # FP32 facet data: relative 1e-4 of each particle's gradient, with a floor at 1e-5 of the largest
+    assert (err <= 1e-4 * scale + 1e-5 * scale.max()).all(), (err / np.maximum(scale, 1e-30)).max()
+
+
+def test_finite_differences_on_random_particles(mix32k, oracle_mod):
+    x, o, w = mix32k
+    x64 = x.astype(np.float64)
+    g, _ = _gpu_grad(x, w, "filter32")
+    noff, nids = oracle_mod.neighbours(o)
+    ell = o["vol"] ** (1.0 / 3.0)
+    rng = np.random.default_rng(5)
+    pick = rng.choice(len(x), 16, replace=False)
+
+    def loss_local(xp, cells):
+        r = oracle_mod.cells(xp, 0.0, 1.0, True, which=cells, mode="certified")
+        return float(np.sum(w[cells] * -np.log(r["vol"])))
+
+    for k in pick:
+        cells = np.unique(np.concatenate([[k], nids[noff[k]:noff[k + 1]]])).astype(np.int64)
+        h0 = 1e-4 * min(1.0, ell[k] / ell.mean())
+        for c in range(3):
+            def fd(h):
+                xp = x64.copy()
+                xm = x64.copy()
+                xp[k, c] += h
+                xm[k, c] -= h
+                return (loss_local(xp % 1.0, cells) - loss_local(xm % 1.0, cells)) / (2 * h)
+            d1, d2 = fd(h0), fd(h0 / 2)
+            rich = (4 * d2 - d1) / 3
+            assert abs(rich - g[k, c]) <= 1e-3 * max(abs(rich), 1e-3 * np.abs(g[k]).max() + 1e-12), (k, c, rich, g[k, c])
+
+
+def test_energy_gradient_matches_oracle(mix32k, oracle_mod):
+    x, o, _ = mix32k
+    pos = torch.from_numpy(x).cuda().requires_grad_(True)
+    vol, energy = vta.cells(pos, (0.0,) * 3, (1.0,) * 3, True, "filter32")
+    energy.sum().backward()
+    g = pos.grad.double().cpu().numpy()
+    ref = oracle_mod.volume_adjoint(o, x.astype(np.float64), g_energy=1.0)
+    scale = np.linalg.norm(ref, axis=1)
+    assert (np.linalg.norm(g - ref, axis=1) <= 1e-3 * scale + 1e-5 * scale.max()).all()
+    e = energy.double().detach().cpu().numpy()
+    assert np.allclose(e, o["mom2"], rtol=1e-4, atol=1e-6 * np.abs(o["mom2"]).max())
+
+
+def test_lloyd_50_steps_energy_decreases():
+    x = torch.from_numpy(inputs.halo_uniform_mix(1048576, L=1.0, seed=3)).cuda()
+    energies = []
+    for _ in range(50):
+        x, E = vta.lloyd_step(x, (0.0,) * 3, (1.0,) * 3)
+        energies.append(E)
+    e = np.array(energies)
+    assert (np.diff(e) <= 1e-5 * e[:-1]).all(), np.diff(e).max()
+    assert e[-1] < 0.9 * e[0]
+
+
+def test_lattice_is_a_lloyd_fixed_point():
+    x = torch.from_numpy(inputs.bcc_lattice(16, dtype=np.float32)).cuda().requires_grad_(True)
+    vol, energy = vta.cells(x, (0.0,) * 3, (1.0,) * 3, True, "filter32")
+    energy.sum().backward()
+    step = x.grad / (2.0 * vol[:, None].detach())
+    assert float(step.abs().max()) < 1e-5 * (1.0 / 16)
