@@ -48,6 +48,7 @@ WORK = {
     "clustered2M": {"n_cert": 150.0, "verts": 26.7, "faces": 15.3},
     "clustered64k": {"n_cert": 175.8, "verts": 26.4, "faces": 15.2},
     "uniform4096": {"n_cert": 42.4, "verts": 27.1, "faces": 15.56},
+    "halosets4096": {"n_cert": 147.19, "verts": 26.55, "faces": 15.27},
 }
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
@@ -75,6 +76,12 @@ def workload(name):
         gen = lambda: inputs.clustered(65536, L=L, seed=1)  # noqa: E731
         desc = dict(workload="clustered 65,536 FP32 points (the 2M recipe scaled), periodic box L=%.4f, seed 1" % L,
                     N=65536, L=L, grid=64)
+    elif name == "halosets4096":
+        x, off = _cached(cache, lambda: inputs.halo_sets())
+        desc = dict(workload="4096 independent NFW halos (c ~ U(5,15), r_vir = 1), sizes log-uniform in "
+                             "[64, 65536], %d FP32 points in all, each set in its own bounded box [-1,1]^3, seed 6"
+                             % len(x), N=len(x), L=2.0, grid=0, set_off=off)
+        return x, desc
     elif name == "uniform4096":
         L = 1.0
         gen = lambda: inputs.uniform(4096, seed=0, dtype=np.float32)  # noqa: E731
@@ -91,6 +98,22 @@ def workload(name):
         except OSError:
             pass
     return x, desc
+
+
+def _cached(cache, gen):
+    """(points, set offsets) from the cache files, else generated and cached."""
+    cache_off = cache[:-4] + "_off.npy"
+    if os.path.exists(cache) and os.path.exists(cache_off):
+        return np.load(cache), np.load(cache_off)
+    x, off = gen()
+    try:
+        np.save(cache + ".tmp.npy", x)
+        np.save(cache_off + ".tmp.npy", off)
+        os.replace(cache + ".tmp.npy", cache)
+        os.replace(cache_off + ".tmp.npy", cache_off)
+    except OSError:
+        pass
+    return x, off
 
 
 class Clocks:
@@ -190,6 +213,23 @@ def cpu_oracle_rate(x, L, n_sample, seed=11):
                                              "built inside the timed call), certified mode, FP64" % (n_sample, len(x)))
 
 
+def cpu_oracle_rate_sets(x, off, n_sample, seed=11):
+    """The FP64 oracle (certified mode, bounded boxes [-1,1]^3) on n_sample cells drawn from all sets."""
+    import oracle
+
+    oracle.build()
+    pick = np.sort(np.random.default_rng(seed).choice(len(x), n_sample, replace=False))
+    sid = np.searchsorted(off, pick, side="right") - 1
+    t0 = time.perf_counter()
+    for s in np.unique(sid):
+        xs = x[off[s]:off[s + 1]].astype(np.float64)
+        oracle.cells(xs, -1.0, 1.0, False, which=pick[sid == s] - off[s], mode="certified")
+    t1 = time.perf_counter()
+    return n_sample / (t1 - t0), dict(cores=os.cpu_count(), seconds=t1 - t0,
+                                      sample="%d random cells drawn from all sets (a k-d tree over each touched set "
+                                             "built inside the timed region), certified mode, FP64" % n_sample)
+
+
 def run_reference(args):
     ws, rank, local = dist_setup(args)
     if rank != 0:
@@ -198,7 +238,10 @@ def run_reference(args):
     rates = []
     info = None
     for k in range(args.warmup + args.steps):
-        r, info = cpu_oracle_rate(x, desc["L"], args.ref_sample, seed=100 + k)
+        if "set_off" in desc:
+            r, info = cpu_oracle_rate_sets(x, desc["set_off"], args.ref_sample, seed=100 + k)
+        else:
+            r, info = cpu_oracle_rate(x, desc["L"], args.ref_sample, seed=100 + k)
         if k >= args.warmup:
             rates.append(r)
     value = statistics.median(rates)
@@ -229,6 +272,8 @@ def run_ours(args):
     x, desc = workload(args.workload)
     N, L, G = desc["N"], desc["L"], desc["grid"]
     box = ((0.0,) * 3, (L,) * 3)
+    set_off = desc.get("set_off")
+    boxes = None if set_off is None else np.tile([-1.0, -1.0, -1.0, 1.0, 1.0, 1.0], (len(set_off) - 1, 1))
     stream = torch.cuda.current_stream(dev)
     xd = torch.from_numpy(x).to(dev)
     w = torch.from_numpy(np.random.default_rng(4).random(N).astype(np.float32)).to(dev)  # dL/dV weights
@@ -237,20 +282,24 @@ def run_ours(args):
     grad = torch.empty(N, 3, dtype=torch.float32, device=dev)
     off = torch.empty(N + 1, dtype=torch.int64, device=dev)
     ids = torch.empty(24 * N, dtype=torch.int32, device=dev)
-    grid = torch.empty(G, G, G, dtype=torch.float32, device=dev)
+    grid = torch.empty(G, G, G, dtype=torch.float32, device=dev) if G else None
     dpos = torch.empty(N, 3, dtype=torch.float32, device=dev)
     stats = []
 
     def step(pos_dev):
         nonlocal ids
-        h = vt.vt_build(pos_dev, None, box[0], box[1], True, args.precision)
+        if set_off is None:
+            h = vt.vt_build(pos_dev, None, box[0], box[1], True, args.precision)
+        else:
+            h = vt.vt_build_batched(pos_dev, set_off, boxes, precision=args.precision)
         nnz = vt.vt_cells(h)
         if nnz > ids.numel():
             ids = torch.empty(int(nnz * 1.2), dtype=torch.int32, device=dev)
         vt.vt_cells(h, vol, off, ids)
         vt.vt_density(h, dens)
         vt.vt_gradient(h, grad)
-        vt.vt_grid_density(h, G, 1, grid)
+        if G:
+            vt.vt_grid_density(h, G, 1, grid)
         vt.vt_backward(h, w, 0.0, dpos)
         st = vt.vt_status(h)
         vt.vt_destroy(h)
@@ -291,7 +340,7 @@ def run_ours(args):
                   dens=torch.empty(N, dtype=torch.float32).pin_memory(),
                   grad=torch.empty(N, 3, dtype=torch.float32).pin_memory(),
                   off=torch.empty(N + 1, dtype=torch.int64).pin_memory(),
-                  grid=torch.empty(G, G, G, dtype=torch.float32).pin_memory(),
+                  grid=torch.empty(G, G, G, dtype=torch.float32).pin_memory() if G else None,
                   dpos=torch.empty(N, 3, dtype=torch.float32).pin_memory())
     ids_h = torch.empty(ids.numel(), dtype=torch.int32).pin_memory()
     xd2 = torch.empty_like(xd)
@@ -303,7 +352,8 @@ def run_ours(args):
         outs_h["dens"].copy_(dens, non_blocking=True)
         outs_h["grad"].copy_(grad, non_blocking=True)
         outs_h["off"].copy_(off, non_blocking=True)
-        outs_h["grid"].copy_(grid, non_blocking=True)
+        if G:
+            outs_h["grid"].copy_(grid, non_blocking=True)
         outs_h["dpos"].copy_(dpos, non_blocking=True)
         ids_h[:n].copy_(ids[:n], non_blocking=True)
         return n
@@ -334,7 +384,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "filter32" else "f64",
             "data": "synthetic",
-            "config": {"workload": desc["workload"], "precision": args.precision, "grid": "%d^3" % G,
+            "config": {"workload": desc["workload"], "precision": args.precision,
+                       "grid": "%d^3" % G if G else "none (no single box)",
                        "parallelism": "replicas" if ws > 1 else "1 GPU",
                        "l2": "inputs and workspaces larger than L2 (no flush)"},
             "fwd_bwd_breakdown_ms": {"build_sort_tree": sort_ms, "build_clip": clip_ms,
@@ -350,8 +401,13 @@ def run_ours(args):
             "clocks": clocks,
             "device_counters": {k: stats[-1][k] for k in ("n_cut", "n_tested", "n_passes", "n_fp64_fallbacks",
                                                           "n_exact_cells", "n_exact_preds", "max_faces")}}
+    if set_off is not None and not args.no_loop_baseline:
+        line["per_set_loop"] = per_set_loop(vt, x, set_off, args.precision, dev, stream, N)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        r, info = cpu_oracle_rate(x, L, args.cpu_sample)
+        if set_off is not None:
+            r, info = cpu_oracle_rate_sets(x, set_off, args.cpu_sample)
+        else:
+            r, info = cpu_oracle_rate(x, L, args.cpu_sample)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                                 "sample": info["sample"]}
     if rank == 0:
@@ -361,6 +417,50 @@ def run_ours(args):
 
         dist.destroy_process_group()
     return 0
+
+
+def per_set_loop(vt, x, set_off, precision, dev, stream, N):
+    """The same batch as a host loop of one vt_build (and the same outputs) per set, timed once after one
+    untimed pass; returns its cells/s."""
+    import torch
+
+    xd = torch.from_numpy(x).to(dev)
+    w = torch.from_numpy(np.random.default_rng(4).random(N).astype(np.float32)).to(dev)
+    vol = torch.empty(N, dtype=torch.float32, device=dev)
+    dens = torch.empty(N, dtype=torch.float32, device=dev)
+    grad = torch.empty(N, 3, dtype=torch.float32, device=dev)
+    dpos = torch.empty(N, 3, dtype=torch.float32, device=dev)
+    lo, hi = (-1.0,) * 3, (1.0,) * 3
+
+    def one_pass():
+        for s in range(len(set_off) - 1):
+            a, b = int(set_off[s]), int(set_off[s + 1])
+            if b == a:
+                continue
+            h = vt.vt_build(xd[a:b], None, lo, hi, False, precision)
+            n = vt.vt_cells(h)
+            off = torch.empty(b - a + 1, dtype=torch.int64, device=dev)
+            ids = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+            vt.vt_cells(h, vol[a:b], off, ids)
+            vt.vt_density(h, dens[a:b])
+            vt.vt_gradient(h, grad[a:b])
+            vt.vt_backward(h, w[a:b], 0.0, dpos[a:b])
+            st = vt.vt_status(h)
+            vt.vt_destroy(h)
+            if st["rc"] != 0:
+                raise RuntimeError("device error %d in set %d" % (st["rc"], s))
+
+    one_pass()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    one_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1)
+    return {"value": N / (t / 1000.0), "unit": UNIT, "ms": t,
+            "what": "host loop of vt_build + vt_cells + vt_density + vt_gradient + vt_backward per set"}
 
 
 def main():
@@ -374,6 +474,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=32768)
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-loop-baseline", action="store_true", help="batched workloads: skip the per-set loop")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -116,6 +116,35 @@ int vt_default_params(vt_params *p);
 int vt_build(vt_handle *h, const void *pos, int dtype, const void *mass, int64_t N, const double box_lo[3],
              const double box_hi[3], int periodic, const vt_params *p, void *stream);
 
+/* most independent sets one vt_build_batched call takes */
+#define VT_MAX_SETS 65536
+
+/*
+ * vt_build_batched -- Voronoi cells of many independent point sets in one
+ * build (Parallel implementation section: the volume is split into
+ * sub-volumes that are tessellated independently; here each set is its own
+ * bounded sub-volume, with no buffer particles, and all sets share one sort,
+ * one search tree and one persistent clipping launch whose work queue runs
+ * over the cells of every set).
+ *   h        host out: new handle (NULL on failure)
+ *   pos      device [N][3], dtype VT_F32 or VT_F64, N = set_off[n_sets]; set s
+ *            is the rows [set_off[s], set_off[s+1]), every coordinate inside
+ *            its own box (walls included)
+ *   mass     device [N] of the same dtype, or NULL for unit masses
+ *   set_off  host [n_sets+1], set_off[0] = 0, non-decreasing (empty sets allowed)
+ *   n_sets   1 .. VT_MAX_SETS
+ *   boxes    host [n_sets][6]: lo x,y,z then hi x,y,z of each set's box; the
+ *            cells of a set are clipped by its box walls (no periodic images)
+ *   p, stream  as for vt_build
+ * A particle's neighbours are particles of its own set only.  The handle
+ * answers vt_cells, vt_density, vt_gradient, vt_moments, vt_backward and
+ * vt_status exactly as a vt_build handle over the concatenated sets would, with
+ * input indices into `pos`; vt_grid_density returns VT_ERR_UNSUPPORTED.
+ * Errors: those of vt_build; VT_ERR_INVALID also for a bad set_off or box.
+ */
+int vt_build_batched(vt_handle *h, const void *pos, int dtype, const void *mass, const int64_t *set_off,
+                     int n_sets, const double *boxes, const vt_params *p, void *stream);
+
 /*
  * vt_cells -- cell volumes and neighbour lists (Implementation section:
  * volume from the facets; neighbours are the particles sharing a facet;
@@ -147,6 +176,7 @@ int vt_gradient(vt_handle h, void *grad);
  * lo + (a + (u+1/2)/S) L/G ..., of the density of the cell containing the
  * sub-point (the nearest particle; ties to the lower index).
  * grid: device [G][G][G] indexed [c][b][a] (x fastest).  1 <= G <= 4096, 1 <= S <= 8.
+ * VT_ERR_UNSUPPORTED on a vt_build_batched handle.
  */
 int vt_grid_density(vt_handle h, int G, int S, void *grid);
 

@@ -81,6 +81,9 @@ def load_library(path: str = LIB_PATH):
     lib.vt_build.argtypes = [ctypes.POINTER(P), P, i32, P, i64, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(vt_params), P]
     lib.vt_build.restype = i32
+    lib.vt_build_batched.argtypes = [ctypes.POINTER(P), P, i32, P, ctypes.POINTER(i64), i32,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vt_params), P]
+    lib.vt_build_batched.restype = i32
     lib.vt_cells.argtypes = [P, P, P, P, ctypes.POINTER(i64)]
     lib.vt_cells.restype = i32
     lib.vt_density.argtypes = [P, P]
@@ -181,13 +184,7 @@ def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), per
     pos = pos.contiguous()
     if mass is not None:
         mass = mass.to(device=pos.device, dtype=pos.dtype).contiguous()
-    p = vt_default_params()
-    p.precision = {"filter32": VT_FILTER32, "plain64": VT_PLAIN64}[precision] if isinstance(precision, str) \
-        else int(precision)
-    p.k_target = int(k_target)
-    p.max_passes = int(max_passes)
-    p.face_pool = int(face_pool)
-    p.reserved[0] = int(radius_policy)
+    p = _params(precision, k_target, max_passes, face_pool, radius_policy)
     lo = (ctypes.c_double * 3)(*[float(v) for v in (box_lo if hasattr(box_lo, "__len__") else (box_lo,) * 3)])
     hi = (ctypes.c_double * 3)(*[float(v) for v in (box_hi if hasattr(box_hi, "__len__") else (box_hi,) * 3)])
     h = ctypes.c_void_p()
@@ -199,6 +196,52 @@ def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), per
         part = ctypes.c_int(-1)
         det = lib.vt_last_error_detail(ctypes.byref(part))
         raise VTError(rc, "vt_build", det, part.value)
+    return Handle(h, pos.shape[0], pos.dtype, pos.device, stream)
+
+
+def _params(precision, k_target, max_passes, face_pool, radius_policy) -> vt_params:
+    p = vt_default_params()
+    p.precision = {"filter32": VT_FILTER32, "plain64": VT_PLAIN64}[precision] if isinstance(precision, str) \
+        else int(precision)
+    p.k_target = int(k_target)
+    p.max_passes = int(max_passes)
+    p.face_pool = int(face_pool)
+    p.reserved[0] = int(radius_policy)
+    return p
+
+
+def vt_build_batched(pos, set_off, boxes, mass=None, precision="filter32", k_target=40, max_passes=1000,
+                     face_pool=24, stream=None, radius_policy=0) -> Handle:
+    """Voronoi cells of independent bounded sets: ``pos`` a CUDA [N,3] tensor, set s the rows
+    [set_off[s], set_off[s+1]) inside ``boxes[s] = (lo x, lo y, lo z, hi x, hi y, hi z)``."""
+    import numpy as np
+    import torch
+
+    lib = load_library()
+    if not (isinstance(pos, torch.Tensor) and pos.is_cuda and pos.dim() == 2 and pos.shape[1] == 3):
+        raise VTError(VT_ERR_INVALID, "vt_build_batched: pos must be a CUDA [N,3] tensor")
+    if pos.dtype not in (torch.float32, torch.float64):
+        raise VTError(VT_ERR_INVALID, "vt_build_batched: pos dtype")
+    pos = pos.contiguous()
+    if mass is not None:
+        mass = mass.to(device=pos.device, dtype=pos.dtype).contiguous()
+    off = np.ascontiguousarray(np.asarray(set_off, dtype=np.int64))
+    bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 6))
+    n_sets = len(off) - 1
+    if n_sets < 1 or bx.shape[0] != n_sets or off[-1] != pos.shape[0]:
+        raise VTError(VT_ERR_INVALID, "vt_build_batched: set_off / boxes / pos sizes disagree")
+    p = _params(precision, k_target, max_passes, face_pool, radius_policy)
+    h = ctypes.c_void_p()
+    dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
+    with torch.cuda.device(pos.device):
+        rc = lib.vt_build_batched(ctypes.byref(h), _ptr(pos), dt, _ptr(mass),
+                                  off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n_sets,
+                                  bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(p),
+                                  _stream_ptr(stream))
+    if rc != VT_OK:
+        part = ctypes.c_int(-1)
+        det = lib.vt_last_error_detail(ctypes.byref(part))
+        raise VTError(rc, "vt_build_batched", det, part.value)
     return Handle(h, pos.shape[0], pos.dtype, pos.device, stream)
 
 

@@ -41,7 +41,7 @@ void free_handle(vt_handle h) {
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     void* ptrs[] = {h->spos, h->perm, h->inv, h->tree_mem, h->cell, h->face_start, h->face_count, h->cstat,
                     h->exact_list, h->dens_sorted, h->faces, h->xws, h->tmp, h->nbr_off_cache, h->dstat,
-                    h->keys, h->keys_alt, h->vals_alt, h->cnt_in};
+                    h->keys, h->keys_alt, h->vals_alt, h->cnt_in, h->sset, h->sgeo, h->soff, h->set_in};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -72,6 +72,9 @@ ClipArgs clip_args(vt_handle h) {
     a.st = h->dstat;
     a.xws = h->xws;
     a.xws_warps = h->xws_warps;
+    a.sset = h->sset;
+    a.sgeo = h->sgeo;
+    a.soff = h->soff;
     return a;
 }
 
@@ -140,13 +143,11 @@ int vt_default_params(vt_params* p) {
     return VT_OK;
 }
 
-int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64_t N, const double box_lo[3],
-             const double box_hi[3], int periodic, const vt_params* p, void* stream) {
-    if (!out) return VT_ERR_INVALID;
-    *out = nullptr;
-    if (!pos || !box_lo || !box_hi || N < 1 || N > 0x7FFFFFFF / 2) return VT_ERR_INVALID;
-    if (dtype != VT_F32 && dtype != VT_F64) return VT_ERR_INVALID;
-    vt_params prm;
+}  // extern "C"
+
+namespace {
+
+int check_params(const vt_params* p, vt_params& prm) {
     vt_default_params(&prm);
     if (p) prm = *p;
     if (prm.precision != VT_PLAIN64 && prm.precision != VT_FILTER32) return VT_ERR_INVALID;
@@ -154,21 +155,30 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     if (prm.k_target < 8 || prm.k_target > 120 || prm.max_passes < 1 || prm.max_passes > 100000 || prm.face_pool < 1 ||
         prm.face_pool > 128)
         return VT_ERR_INVALID;
-    Geometry geo;
+    return VT_OK;
+}
+
+int make_geometry(const double* lo, const double* hi, int periodic, int precision, Geometry& geo) {
     memset(&geo, 0, sizeof(geo));
     for (int c = 0; c < 3; c++) {
-        if (!(box_hi[c] > box_lo[c]) || !isfinite(box_lo[c]) || !isfinite(box_hi[c])) return VT_ERR_INVALID;
-        geo.lo[c] = box_lo[c];
-        geo.hi[c] = box_hi[c];
-        geo.L[c] = box_hi[c] - box_lo[c];
+        if (!(hi[c] > lo[c]) || !isfinite(lo[c]) || !isfinite(hi[c])) return VT_ERR_INVALID;
+        geo.lo[c] = lo[c];
+        geo.hi[c] = hi[c];
+        geo.L[c] = hi[c] - lo[c];
         geo.Lf[c] = (float)geo.L[c];
         geo.halfLf[c] = 0.5f * geo.Lf[c];
-        geo.lof[c] = (float)box_lo[c];
-        geo.hif[c] = (float)box_hi[c];
-        if (prm.precision == VT_FILTER32 && periodic && (double)geo.Lf[c] != geo.L[c]) return VT_ERR_UNSUPPORTED;
+        geo.lof[c] = (float)lo[c];
+        geo.hif[c] = (float)hi[c];
+        if (precision == VT_FILTER32 && periodic && (double)geo.Lf[c] != geo.L[c]) return VT_ERR_UNSUPPORTED;
     }
     geo.periodic = periodic ? 1 : 0;
+    return VT_OK;
+}
 
+// Shared by vt_build (n_sets == 0: one set, geometry `geo`) and vt_build_batched (n_sets >= 1: the host
+// tables set_off [n_sets+1] and sgeo [n_sets]).
+int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int64_t N, const Geometry& geo,
+               int n_sets, const int64_t* set_off, const Geometry* sgeo_host, const vt_params& prm, void* stream) {
     vt_handle h = new (std::nothrow) vt_handle_s;
     if (!h) return VT_ERR_OOM;
     memset(h, 0, sizeof(*h));
@@ -177,6 +187,7 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     h->precision = prm.precision;
     h->prm = prm;
     h->geo = geo;
+    h->n_sets = n_sets;
     h->stream = (cudaStream_t)stream;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -211,6 +222,12 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     h->tmp_bytes = tb > sb ? tb : sb;
     h->tmp = A.get<unsigned char>(h->tmp_bytes);
     h->dstat = A.get<DevStatus>(1);
+    if (n_sets > 0) {
+        h->sset = A.get<uint32_t>(N);
+        h->set_in = A.get<uint32_t>(N);
+        h->sgeo = A.get<Geometry>(n_sets);
+        h->soff = A.get<int64_t>(n_sets + 1);
+    }
     for (int k = 0; k < 4; k++)
         if (cudaEventCreate(&h->ev[k]) != cudaSuccess) {
             cudaGetLastError();
@@ -224,10 +241,26 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     cudaStream_t s = h->stream;
     memset(&h->hstat, 0, sizeof(h->hstat));
     int rc = cuda_rc(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), s));
+    if (!rc && n_sets > 0) {
+        rc = cuda_rc(cudaMemcpyAsync(h->sgeo, sgeo_host, n_sets * sizeof(Geometry), cudaMemcpyHostToDevice, s));
+        if (!rc)
+            rc = cuda_rc(cudaMemcpyAsync(h->soff, set_off, (n_sets + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
     if (!rc) {
         cudaEventRecord(h->ev[0], s);
-        h->n_launches += launch_key(pos, dtype, N, geo, h->keys, h->perm, h->dstat, s);
-        h->n_launches += radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48, h->tmp, s);
+        if (n_sets > 0) {
+            // sort key = set id above the 48-bit Morton code of the set's own box: the sets stay contiguous
+            // and in order, so set s occupies the same index range [set_off[s], set_off[s+1]) after sorting
+            int sbits = 0;
+            while ((1 << sbits) < n_sets) sbits++;
+            h->n_launches += launch_set_ids(h->soff, n_sets, N, h->set_in, s);
+            h->n_launches += launch_key_batched(pos, dtype, N, h->sgeo, h->set_in, h->keys, h->perm, h->dstat, s);
+            h->n_launches += radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48 + sbits, h->tmp, s);
+            h->n_launches += launch_gather_u32(h->set_in, h->perm, N, h->sset, s);
+        } else {
+            h->n_launches += launch_key(pos, dtype, N, geo, h->keys, h->perm, h->dstat, s);
+            h->n_launches += radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48, h->tmp, s);
+        }
         h->n_launches += launch_gather(pos, mass, dtype, h->perm, N, h->spos, h->inv, s);
         h->n_launches += launch_tree(h->spos, dtype, N, h->tree, s);
         cudaEventRecord(h->ev[1], s);
@@ -257,6 +290,47 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     h->n_faces = (int64_t)h->hstat.n_faces;
     *out = h;
     return VT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64_t N, const double box_lo[3],
+             const double box_hi[3], int periodic, const vt_params* p, void* stream) {
+    if (!out) return VT_ERR_INVALID;
+    *out = nullptr;
+    if (!pos || !box_lo || !box_hi || N < 1 || N > 0x7FFFFFFF / 2) return VT_ERR_INVALID;
+    if (dtype != VT_F32 && dtype != VT_F64) return VT_ERR_INVALID;
+    vt_params prm;
+    int rc = check_params(p, prm);
+    if (rc) return rc;
+    Geometry geo;
+    rc = make_geometry(box_lo, box_hi, periodic, prm.precision, geo);
+    if (rc) return rc;
+    return build_impl(out, pos, dtype, mass, N, geo, 0, nullptr, nullptr, prm, stream);
+}
+
+int vt_build_batched(vt_handle* out, const void* pos, int dtype, const void* mass, const int64_t* set_off, int n_sets,
+                     const double* boxes, const vt_params* p, void* stream) {
+    if (!out) return VT_ERR_INVALID;
+    *out = nullptr;
+    if (!pos || !set_off || !boxes || n_sets < 1 || n_sets > VT_MAX_SETS) return VT_ERR_INVALID;
+    if (dtype != VT_F32 && dtype != VT_F64) return VT_ERR_INVALID;
+    if (set_off[0] != 0) return VT_ERR_INVALID;
+    for (int k = 0; k < n_sets; k++)
+        if (set_off[k + 1] < set_off[k]) return VT_ERR_INVALID;
+    const int64_t N = set_off[n_sets];
+    if (N < 1 || N > 0x7FFFFFFF / 2) return VT_ERR_INVALID;
+    vt_params prm;
+    int rc = check_params(p, prm);
+    if (rc) return rc;
+    Geometry* sg = new (std::nothrow) Geometry[n_sets];
+    if (!sg) return VT_ERR_OOM;
+    for (int k = 0; k < n_sets && !rc; k++) rc = make_geometry(boxes + 6 * k, boxes + 6 * k + 3, 0, prm.precision, sg[k]);
+    if (!rc) rc = build_impl(out, pos, dtype, mass, N, sg[0], n_sets, set_off, sg, prm, stream);
+    delete[] sg;
+    return rc;
 }
 
 int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t* n_faces_out) {
@@ -302,6 +376,7 @@ int vt_gradient(vt_handle h, void* grad) {
 int vt_grid_density(vt_handle h, int G, int S, void* grid) {
     if (!h || !grid || G < 1 || G > 4096 || S < 1 || S > 8) return VT_ERR_INVALID;
     if ((int64_t)G * G * G > ((int64_t)1 << 34)) return VT_ERR_INVALID;
+    if (h->n_sets > 0) return VT_ERR_UNSUPPORTED;  // a grid needs one box
     int rc = ensure_density(h);
     if (rc) return rc;
     h->n_launches += launch_grid(h->spos, h->dtype, h->N, h->geo, h->faces, h->face_start, h->face_count, h->keys,

@@ -823,7 +823,8 @@ __device__ __forceinline__ float axis_gap(float q, float lo, float hi, float L, 
 // first Cap::CAND are stored) or -2 on stack overflow.
 template <typename P, typename CT, int TP>
 __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geometry& g, const Tree& t, uint32_t self,
-                       const P& pi, CT rlo2, CT rhi2, const float* bmin, const float* bmax) {
+                       const P& pi, CT rlo2, CT rhi2, const float* bmin, const float* bmax, int64_t slo,
+                       int64_t shi) {
     const unsigned lane = lane_id(), lt = lanemask_lt();
     for (int k = (int)lane; k < HIST_BINS; k += 32) S.hist[k] = 0u;
     __syncwarp();
@@ -849,7 +850,8 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
     {
         int64_t nt = t.count[top];
         bool hit = false;
-        if ((int64_t)lane < nt) {
+        const int64_t span_top = (int64_t)1 << (5 * top);
+        if ((int64_t)lane < nt && lane * span_top < shi && (lane + 1) * span_top > slo) {
             float4 lo = t.lo[t.off[top] + lane], hi = t.hi[t.off[top] + lane];
             float dx = fmaxf(axis_gap(qx, lo.x, hi.x, g.Lf[0], g.periodic) - slack, 0.f);
             float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], g.periodic) - slack, 0.f);
@@ -880,7 +882,7 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
             unsigned long long key = 0ull;
             CT d2 = (CT)0, dx = (CT)0, dy = (CT)0, dz = (CT)0;
             int code = 13;
-            if (j < N && (uint32_t)j != self) {
+            if (j >= slo && j < shi && (uint32_t)j != self) {
                 P pj = spos[j];
                 DispF<P, CT>::get(pj, pi, g, dx, dy, dz, code);
                 d2 = f_fma<CT>(dz, dz, f_fma<CT>(dy, dy, dx * dx));
@@ -914,7 +916,8 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
             int cl = lvl - 1;
             int64_t c = node * 32 + lane;
             bool hit = false;
-            if (c < t.count[cl]) {
+            const int64_t span = (int64_t)1 << (5 * cl);  // sorted particles under a node of level cl
+            if (c < t.count[cl] && c * span < shi && (c + 1) * span > slo) {
                 float4 lo = t.lo[t.off[cl] + c], hi = t.hi[t.off[cl] + c];
                 float dx = fmaxf(axis_gap(qx, lo.x, hi.x, g.Lf[0], g.periodic) - slack, 0.f);
                 float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], g.periodic) - slack, 0.f);
@@ -1010,7 +1013,15 @@ template <typename P, typename CT, bool EXACT, int TP>
 __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, double* xws, CellCounters& cc,
                        bool small_box) {
     const P* spos = (const P*)A.spos;
-    const Geometry& g = A.geo;
+    // geometry and sorted index range of the cell's point set
+    Geometry g = A.geo;
+    int64_t slo = 0, shi = A.N;
+    if (A.sset) {
+        const uint32_t s = A.sset[self];
+        g = A.sgeo[s];
+        slo = A.soff[s];
+        shi = A.soff[s + 1];
+    }
     const unsigned lane = lane_id(), lt = lanemask_lt();
     const CT u = Prec<CT>::u();
     const P pi = spos[self];
@@ -1025,7 +1036,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         int64_t b0 = ((int64_t)self / 32) * 32;
         int64_t j = b0 + lane;
         float d2f = INFINITY;
-        if (j < A.N && (uint32_t)j != self) {
+        if (j >= slo && j < shi && (uint32_t)j != self) {
             P pj = spos[j];
             CT dx, dy, dz;
             int code;
@@ -1048,7 +1059,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             if (mx > 0.f) dk = mx;
             else {
                 double vol = g.L[0] * g.L[1] * g.L[2];
-                double sp = cbrt(vol / (double)A.N);
+                double sp = cbrt(vol / (double)(shi - slo));
                 dk = (float)(4.0 * sp * sp);
             }
         }
@@ -1139,7 +1150,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         int cnt = -1;
         VT_T0(tc0);
         for (int shrink = 0; shrink < 64; shrink++) {
-            cnt = collect<P, CT, TP>(S, spos, A.N, g, A.tree, self, pi, rlo2, rhi2, bmin, bmax);
+            cnt = collect<P, CT, TP>(S, spos, A.N, g, A.tree, self, pi, rlo2, rhi2, bmin, bmax, slo, shi);
             cc.n_collect++;
             if (cnt > 0) cc.n_collected += cnt;
             if (cnt == -2) return CAP_STACK;

@@ -79,8 +79,14 @@ struct vt_handle_s {
     int dtype;  // VT_F32 / VT_F64
     int precision;
     vt_params prm;
-    vt::Geometry geo;
+    vt::Geometry geo;   // the box (batched handles: the first set's box, not periodic)
     cudaStream_t stream;
+    // batched independent sets (n_sets == 0 for vt_build)
+    int n_sets;
+    uint32_t* sset;     // [N] set of each sorted particle
+    uint32_t* set_in;   // [N] set of each input particle
+    vt::Geometry* sgeo; // [n_sets]
+    int64_t* soff;      // [n_sets+1] index range of each set (input and sorted order alike)
     // sorted particles
     void* spos;         // float4 (f32) or double4-like 4 doubles (f64): x,y,z,m
     uint32_t* perm;     // sorted -> input index

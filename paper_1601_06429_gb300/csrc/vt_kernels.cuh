@@ -22,6 +22,10 @@ int launch_key(const void* pos, int dtype, int64_t N, const Geometry& g, uint64_
                 cudaStream_t s);
 int launch_gather(const void* pos, const void* mass, int dtype, const uint32_t* perm, int64_t N, void* spos,
                    uint32_t* inv, cudaStream_t s);
+int launch_key_batched(const void* pos, int dtype, int64_t N, const Geometry* sgeo, const uint32_t* setid,
+                       uint64_t* key, uint32_t* idx, DevStatus* st, cudaStream_t s);
+int launch_set_ids(const int64_t* soff, int n_sets, int64_t N, uint32_t* setid, cudaStream_t s);
+int launch_gather_u32(const uint32_t* src, const uint32_t* perm, int64_t N, uint32_t* dst, cudaStream_t s);
 void tree_layout(int64_t N, Tree& t);
 int launch_tree(const void* spos, int dtype, int64_t N, Tree& t, cudaStream_t s);
 
@@ -44,6 +48,11 @@ struct ClipArgs {
     DevStatus* st;
     double* xws;   // exact workspace, per warp
     int xws_warps;
+    // batched independent sets (NULL for one set): set of each sorted particle, geometry of each set, and the
+    // sorted index range [soff[s], soff[s+1]) of each set
+    const uint32_t* sset;
+    const Geometry* sgeo;
+    const int64_t* soff;
 };
 int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s);
 int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);

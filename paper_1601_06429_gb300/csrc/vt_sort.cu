@@ -49,6 +49,71 @@ __global__ void k_key(const T* __restrict__ pos, int64_t N, Geometry g, uint64_t
     idx[i] = (uint32_t)i;
 }
 
+// batched sets: key = set << 48 | Morton code of the position quantised in the set's own box
+template <typename T>
+__global__ void k_key_batched(const T* __restrict__ pos, int64_t N, const Geometry* __restrict__ sgeo,
+                              const uint32_t* __restrict__ setid, uint64_t* __restrict__ key,
+                              uint32_t* __restrict__ idx, DevStatus* st) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const uint32_t s = setid[i];
+    const Geometry& g = sgeo[s];
+    uint32_t q[3];
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        double x = (double)pos[3 * i + c];
+        bool ok = g.periodic ? (x >= g.lo[c] && x < g.hi[c]) : (x >= g.lo[c] && x <= g.hi[c]);
+        if (!ok) bad = true;
+        double t = (x - g.lo[c]) / g.L[c] * 65536.0;
+        int qi = ok ? (int)t : 0;
+        q[c] = (uint32_t)min(max(qi, 0), 65535);
+    }
+    if (bad) {
+        atomicAdd(&st->invalid_input, 1u);
+        atomicCAS(&st->error, 0, VT_ERR_INVALID);
+    }
+    key[i] = ((uint64_t)s << 48) | spread3_16(q[0]) | (spread3_16(q[1]) << 1) | (spread3_16(q[2]) << 2);
+    idx[i] = (uint32_t)i;
+}
+
+// set of every particle from the set offsets (binary search)
+__global__ void k_set_ids(const int64_t* __restrict__ soff, int n_sets, int64_t N, uint32_t* __restrict__ setid) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int lo = 0, hi = n_sets;  // soff[lo] <= i < soff[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (soff[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    setid[i] = (uint32_t)lo;
+}
+
+__global__ void k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ perm, int64_t N,
+                             uint32_t* __restrict__ dst) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) dst[k] = src[perm[k]];
+}
+
+int launch_key_batched(const void* pos, int dtype, int64_t N, const Geometry* sgeo, const uint32_t* setid,
+                       uint64_t* key, uint32_t* idx, DevStatus* st, cudaStream_t s) {
+    unsigned nb = (unsigned)((N + 255) / 256);
+    if (dtype == VT_F32)
+        k_key_batched<float><<<nb, 256, 0, s>>>((const float*)pos, N, sgeo, setid, key, idx, st);
+    else
+        k_key_batched<double><<<nb, 256, 0, s>>>((const double*)pos, N, sgeo, setid, key, idx, st);
+    return 1;
+}
+int launch_set_ids(const int64_t* soff, int n_sets, int64_t N, uint32_t* setid, cudaStream_t s) {
+    k_set_ids<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(soff, n_sets, N, setid);
+    return 1;
+}
+int launch_gather_u32(const uint32_t* src, const uint32_t* perm, int64_t N, uint32_t* dst, cudaStream_t s) {
+    k_gather_u32<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(src, perm, N, dst);
+    return 1;
+}
+
 // ---------------------------------------------------------------- scan
 // exclusive scan, blocks of 1024 threads x 4 items, recursive over block sums
 template <typename TI, typename TO>
