@@ -50,6 +50,9 @@ WORK = {
     "uniform4096": {"n_cert": 42.4, "verts": 27.1, "faces": 15.56},
     "halosets4096": {"n_cert": 147.19, "verts": 26.55, "faces": 15.27},
 }
+# DRAM bytes (read + write) of one launch of the clipping kernel, from one ncu capture of this kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/launches_clustered16M.md)
+CLIP_TRAFFIC = {"clustered16M": 10.631e9}
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
 
@@ -394,7 +397,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": CLIP_TRAFFIC.get(args.workload),
                          "kernel": "k_clip (clipping, security test, facet emission)",
                          "work": "%.0f algorithmic flops/cell x %d cells per launch" % (fpc, N),
                          "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"},

@@ -116,6 +116,25 @@ int vt_default_params(vt_params *p);
 int vt_build(vt_handle *h, const void *pos, int dtype, const void *mass, int64_t N, const double box_lo[3],
              const double box_hi[3], int periodic, const vt_params *p, void *stream);
 
+/*
+ * vt_rebuild -- the cells of new positions for the same particles, in the
+ * handle's workspace (the tessellation step again, e.g. for the next Lloyd
+ * iteration or the next batch of sets of the same sizes).
+ *   pos   device [N][3], the handle's N and dtype; a batched handle keeps its
+ *         set offsets and boxes
+ *   mass  device [N] or NULL for unit masses
+ * Allocates nothing and does not synchronise: every step is a kernel launch or
+ * an asynchronous device memset on the handle's stream, so the call may be
+ * captured in a CUDA graph (make the vt_build that created the handle before
+ * the capture).  Errors found on the device are sticky and come back from
+ * vt_status: VT_ERR_INVALID (NaN or out-of-box coordinates; no cell is
+ * computed), VT_ERR_CAPACITY (the facet pool of the handle is full: build a
+ * new handle, with a larger vt_params.face_pool), VT_ERR_DUPLICATE,
+ * VT_ERR_SECURITY, VT_ERR_NUMERIC.  Returns VT_ERR_INVALID (NULL argument) or
+ * VT_ERR_CUDA (a launch failed), else VT_OK.
+ */
+int vt_rebuild(vt_handle h, const void *pos, const void *mass);
+
 /* most independent sets one vt_build_batched call takes */
 #define VT_MAX_SETS 65536
 
@@ -154,7 +173,10 @@ int vt_build_batched(vt_handle *h, const void *pos, int dtype, const void *mass,
  *   nbr_id       device int32 [nnz]: neighbours of particle i, ascending, at
  *                nbr_id[nbr_off[i] .. nbr_off[i+1]); NULL = size query
  *   n_faces_out  host out: nnz (always written when non-NULL; the size query
- *                needs no synchronisation: the count is known after vt_build)
+ *                needs no synchronisation on a handle that was never passed to
+ *                vt_rebuild, and synchronises the handle's stream on one that was)
+ * After a vt_rebuild, nbr_id needs room for the new nnz: ask for it first.
+ * Inside a stream capture pass nbr_id = NULL and n_faces_out = NULL.
  */
 int vt_cells(vt_handle h, void *vol, int64_t *nbr_off, int32_t *nbr_id, int64_t *n_faces_out);
 

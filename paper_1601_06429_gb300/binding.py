@@ -84,6 +84,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_build_batched.argtypes = [ctypes.POINTER(P), P, i32, P, ctypes.POINTER(i64), i32,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vt_params), P]
     lib.vt_build_batched.restype = i32
+    lib.vt_rebuild.argtypes = [P, P, P]
+    lib.vt_rebuild.restype = i32
     lib.vt_cells.argtypes = [P, P, P, P, ctypes.POINTER(i64)]
     lib.vt_cells.restype = i32
     lib.vt_density.argtypes = [P, P]
@@ -245,11 +247,27 @@ def vt_build_batched(pos, set_off, boxes, mass=None, precision="filter32", k_tar
     return Handle(h, pos.shape[0], pos.dtype, pos.device, stream)
 
 
-def vt_cells(h: Handle, vol=None, nbr_off=None, nbr_id=None) -> int:
-    """Fill any of ``vol`` [N], ``nbr_off`` int64 [N+1], ``nbr_id`` int32 [nnz]; returns nnz."""
+def vt_rebuild(h: Handle, pos, mass=None) -> None:
+    """New positions for the handle's particles (same N, dtype and sets); no allocation, no synchronisation,
+    so the call can be captured in a CUDA graph.  Device-side errors come back from vt_status."""
+    import torch
+
+    if not (isinstance(pos, torch.Tensor) and pos.is_cuda and tuple(pos.shape) == (h.N, 3) and pos.dtype == h.dtype
+            and pos.is_contiguous()):
+        raise VTError(VT_ERR_INVALID, "vt_rebuild: pos must be a contiguous CUDA [N,3] tensor of the handle's dtype")
+    if mass is not None and not (isinstance(mass, torch.Tensor) and mass.is_cuda and mass.dtype == h.dtype
+                                 and mass.is_contiguous() and mass.numel() == h.N):
+        raise VTError(VT_ERR_INVALID, "vt_rebuild: mass must be a contiguous CUDA [N] tensor of the handle's dtype")
+    _check(load_library().vt_rebuild(h.ptr, _ptr(pos), _ptr(mass)), "vt_rebuild")
+
+
+def vt_cells(h: Handle, vol=None, nbr_off=None, nbr_id=None, count=True):
+    """Fill any of ``vol`` [N], ``nbr_off`` int64 [N+1], ``nbr_id`` int32 [nnz]; returns nnz (None with
+    ``count=False``, the form to use inside a CUDA graph capture)."""
     n = ctypes.c_int64(0)
-    _check(load_library().vt_cells(h.ptr, _ptr(vol), _ptr(nbr_off), _ptr(nbr_id), ctypes.byref(n)), "vt_cells")
-    return int(n.value)
+    _check(load_library().vt_cells(h.ptr, _ptr(vol), _ptr(nbr_off), _ptr(nbr_id),
+                                   ctypes.byref(n) if count else None), "vt_cells")
+    return int(n.value) if count else None
 
 
 def vt_density(h: Handle, dens) -> None:

@@ -120,7 +120,8 @@ int run_clip(vt_handle h) {
     return VT_ERR_CAPACITY;
 }
 
-__global__ void k_set_i64(int64_t* p, int64_t v) { *p = v; }
+// the last neighbour offset = the facet count of the last clipping run
+__global__ void k_off_tail(int64_t* p, const DevStatus* st) { *p = (int64_t)st->n_faces; }
 
 int ensure_density(vt_handle h) {
     if (h->dens_ready) return VT_OK;
@@ -173,6 +174,27 @@ int make_geometry(const double* lo, const double* hi, int periodic, int precisio
     }
     geo.periodic = periodic ? 1 : 0;
     return VT_OK;
+}
+
+// Key, sort, gather and tree of the positions `pos` into the handle's workspace (no allocation, no
+// synchronisation).
+void enqueue_sort_tree(vt_handle h, const void* pos, const void* mass) {
+    cudaStream_t s = h->stream;
+    const int64_t N = h->N;
+    if (h->n_sets > 0) {
+        // sort key = set id above the 48-bit Morton code of the set's own box: the sets stay contiguous
+        // and in order, so set s occupies the same index range [set_off[s], set_off[s+1]) after sorting
+        int sbits = 0;
+        while ((1 << sbits) < h->n_sets) sbits++;
+        h->n_launches += launch_key_batched(pos, h->dtype, N, h->sgeo, h->set_in, h->keys, h->perm, h->dstat, s);
+        h->n_launches += radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48 + sbits, h->tmp, s);
+        h->n_launches += launch_gather_u32(h->set_in, h->perm, N, h->sset, s);
+    } else {
+        h->n_launches += launch_key(pos, h->dtype, N, h->geo, h->keys, h->perm, h->dstat, s);
+        h->n_launches += radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48, h->tmp, s);
+    }
+    h->n_launches += launch_gather(pos, mass, h->dtype, h->perm, N, h->spos, h->inv, s);
+    h->n_launches += launch_tree(h->spos, h->dtype, N, h->tree, s);
 }
 
 // Shared by vt_build (n_sets == 0: one set, geometry `geo`) and vt_build_batched (n_sets >= 1: the host
@@ -248,21 +270,8 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
     }
     if (!rc) {
         cudaEventRecord(h->ev[0], s);
-        if (n_sets > 0) {
-            // sort key = set id above the 48-bit Morton code of the set's own box: the sets stay contiguous
-            // and in order, so set s occupies the same index range [set_off[s], set_off[s+1]) after sorting
-            int sbits = 0;
-            while ((1 << sbits) < n_sets) sbits++;
-            h->n_launches += launch_set_ids(h->soff, n_sets, N, h->set_in, s);
-            h->n_launches += launch_key_batched(pos, dtype, N, h->sgeo, h->set_in, h->keys, h->perm, h->dstat, s);
-            h->n_launches += radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48 + sbits, h->tmp, s);
-            h->n_launches += launch_gather_u32(h->set_in, h->perm, N, h->sset, s);
-        } else {
-            h->n_launches += launch_key(pos, dtype, N, geo, h->keys, h->perm, h->dstat, s);
-            h->n_launches += radix_sort(h->keys, h->perm, h->keys_alt, h->vals_alt, N, 48, h->tmp, s);
-        }
-        h->n_launches += launch_gather(pos, mass, dtype, h->perm, N, h->spos, h->inv, s);
-        h->n_launches += launch_tree(h->spos, dtype, N, h->tree, s);
+        if (n_sets > 0) h->n_launches += launch_set_ids(h->soff, n_sets, N, h->set_in, s);
+        enqueue_sort_tree(h, pos, mass);
         cudaEventRecord(h->ev[1], s);
         rc = cuda_rc(cudaGetLastError());
     }
@@ -333,10 +342,34 @@ int vt_build_batched(vt_handle* out, const void* pos, int dtype, const void* mas
     return rc;
 }
 
+int vt_rebuild(vt_handle h, const void* pos, const void* mass) {
+    if (!h || !pos) return VT_ERR_INVALID;
+    cudaStream_t s = h->stream;
+    // every counter, the work queues and the sticky error start at zero
+    int rc = cuda_rc(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), s));
+    if (rc) return rc;
+    enqueue_sort_tree(h, pos, mass);
+    ClipArgs a = clip_args(h);
+    h->n_launches += launch_clip(a, h->dtype, h->precision, h->sm_count, s);
+    h->n_launches += launch_clip_exact(a, h->dtype, h->sm_count, s);
+    h->dens_ready = 0;
+    h->faces_on_device = 1;
+    return cuda_rc(cudaGetLastError());
+}
+
 int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t* n_faces_out) {
     if (!h) return VT_ERR_INVALID;
     cudaStream_t s = h->stream;
-    if (n_faces_out) *n_faces_out = h->n_faces;
+    if (n_faces_out) {
+        if (h->faces_on_device) {
+            // once the handle has been rebuilt (perhaps by a replayed graph) the count is read from the device
+            int rc = cuda_rc(cudaMemcpyAsync(&h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+            if (!rc) rc = cuda_rc(cudaStreamSynchronize(s));
+            if (rc) return rc;
+            h->n_faces = (int64_t)h->hstat.n_faces;
+        }
+        *n_faces_out = h->n_faces;
+    }
     if (vol) h->n_launches += launch_out_vol(h->cell, h->perm, h->N, vol, h->dtype, s);
     if (nbr_off || nbr_id) {
         int64_t* off = nbr_off;
@@ -350,7 +383,7 @@ int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t*
         }
         h->n_launches += launch_nbr_count(h->face_count, h->inv, h->N, h->cnt_in, s);
         h->n_launches += scan_u16_i64(h->cnt_in, off, h->N, h->tmp, s);
-        k_set_i64<<<1, 1, 0, s>>>(off + h->N, h->n_faces);
+        k_off_tail<<<1, 1, 0, s>>>(off + h->N, h->dstat);
         h->n_launches += 1;
         if (nbr_id)
             h->n_launches += launch_nbr_emit(h->faces, h->face_start, h->face_count, h->perm, h->inv, off, h->N, nbr_id, s);
@@ -414,6 +447,8 @@ int vt_status(vt_handle h, vt_stats* out) {
     out->n_exact_preds = (int64_t)d.n_exact_preds;
     out->n_exact_zero = (int64_t)d.n_exact_zero;
     out->max_faces = (int64_t)d.max_faces;
+    if (d.error == RC_POOL_HOST) d.error = VT_ERR_CAPACITY;  // facet pool full in a vt_rebuild
+    if (d.invalid_input && !d.error) d.error = VT_ERR_INVALID;
     out->device_error = d.error;
     out->n_launches = h->n_launches;
     out->t_sort_ms = h->t_sort_ms;

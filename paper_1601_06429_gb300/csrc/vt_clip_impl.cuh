@@ -1436,6 +1436,8 @@ __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
     WarpSmem<CT, TP>& S = reinterpret_cast<WarpSmem<CT, TP>*>(smem_raw)[w];
     const int gw = blockIdx.x * WPB + w;
     double* xws = EXACT ? (A.xws + (size_t)gw * EXACT_WS) : nullptr;
+    // rejected input (NaN or out-of-box coordinates, recorded by the key kernel before this launch): no cells
+    if (*((volatile unsigned*)&A.st->invalid_input)) return;
     CellCounters cc = {};
     const uint32_t total = EXACT ? 0u : (uint32_t)A.N;
     for (;;) {
@@ -1510,10 +1512,18 @@ static void launch_one(const ClipArgs& a, int sm_count, cudaStream_t s) {
     constexpr int TP = EXACT ? 16 : 4;
     constexpr int WPB = EXACT ? 1 : CLIP_WARPS;
     size_t smem = sizeof(WarpSmem<CT, TP>) * WPB;
-    cudaFuncSetAttribute(k_clip<P, CT, EXACT, TP, WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip<P, CT, EXACT, TP, WPB>, WPB * 32, smem);
-    if (per_sm < 1) per_sm = 1;
+    // the shared-memory attribute and the occupancy are set up once per device (no such call is made while a
+    // stream is being captured, after the first launch)
+    static int per_sm_dev[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = (dev >= 0 && dev < 64) ? per_sm_dev[dev] : 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_clip<P, CT, EXACT, TP, WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip<P, CT, EXACT, TP, WPB>, WPB * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        if (dev >= 0 && dev < 64) per_sm_dev[dev] = per_sm;
+    }
     int blocks = sm_count * per_sm;
     if (EXACT) blocks = a.xws_warps < blocks ? a.xws_warps : blocks;
     k_clip<P, CT, EXACT, TP, WPB><<<blocks, WPB * 32, smem, s>>>(a);

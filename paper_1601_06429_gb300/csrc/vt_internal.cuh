@@ -119,6 +119,7 @@ struct vt_handle_s {
     vt::DevStatus* dstat;   // device
     vt::DevStatus hstat;    // host copy after build
     int64_t n_faces;
+    int faces_on_device;    // set by vt_rebuild: the facet count is read from the device from then on
     int sm_count;
     int64_t n_launches;
     double t_sort_ms, t_clip_ms;
