@@ -403,7 +403,8 @@ def run_ours(args):
                          "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"},
             "clocks": clocks,
             "device_counters": {k: stats[-1][k] for k in ("n_cut", "n_tested", "n_passes", "n_fp64_fallbacks",
-                                                          "n_exact_cells", "n_exact_preds", "max_faces")}}
+                                                          "n_exact_cells", "n_exact_preds", "max_faces",
+                                                          "n_handed_over", "n_bucket_passes")}}
     if set_off is not None and not args.no_loop_baseline:
         line["per_set_loop"] = per_set_loop(vt, x, set_off, args.precision, dev, stream, N)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

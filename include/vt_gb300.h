@@ -67,7 +67,10 @@ typedef struct vt_params {
     int k_target;   /* particles aimed for in a cell's first candidate pass (default 40) */
     int max_passes; /* candidate radius passes per cell before VT_ERR_SECURITY (default 1000) */
     int face_pool;  /* facet records reserved per particle (default 24; grown on demand) */
-    int reserved[4]; /* [0]: candidate pass sizing, 0 = radius doubling up to 2R (default), 1 = also limited
+    int threads_per_cell; /* VT_FILTER32 only: 32 = one warp per cell (default; 0 means 32); 1 = one thread
+                             per cell first, 32 cells of a search-tree bucket per warp, the cells it cannot
+                             finish then taken by a warp each (same results) */
+    int reserved[3]; /* [0]: candidate pass sizing, 0 = radius doubling up to 2R (default), 1 = also limited
                         by the density seen so far; others must be 0 */
 } vt_params;
 
@@ -89,6 +92,8 @@ typedef struct vt_stats {
     double t_clip_ms;         /* device time of vt_build's clipping kernels, last attempt (CUDA events) */
     int64_t reserved[3];      /* diagnostics: [0] internal detail of device_error, [1] candidate collections,
                                  [2] candidates collected */
+    int64_t n_handed_over;    /* FP32 filter: cells the thread-per-cell kernel handed to the warp-per-cell kernel */
+    int64_t n_bucket_passes;  /* FP32 filter: radius passes of the thread-per-cell kernel, summed over buckets */
 } vt_stats;
 
 typedef struct vt_handle_s *vt_handle;

@@ -32,7 +32,7 @@ VT_FILTER32 = 1
 
 class vt_params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("k_target", ctypes.c_int), ("max_passes", ctypes.c_int),
-                ("face_pool", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("face_pool", ctypes.c_int), ("threads_per_cell", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class vt_stats(ctypes.Structure):
@@ -41,7 +41,8 @@ class vt_stats(ctypes.Structure):
                 ("n_exact_cells", ctypes.c_int64), ("n_exact_preds", ctypes.c_int64),
                 ("n_exact_zero", ctypes.c_int64), ("max_faces", ctypes.c_int64), ("device_error", ctypes.c_int32),
                 ("error_particle", ctypes.c_int32), ("n_launches", ctypes.c_int64), ("t_sort_ms", ctypes.c_double),
-                ("t_clip_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
+                ("t_clip_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 3), ("n_handed_over", ctypes.c_int64),
+                ("n_bucket_passes", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -174,7 +175,7 @@ class Handle:
 
 
 def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), periodic=True, precision="filter32",
-             k_target=40, max_passes=1000, face_pool=24, stream=None, radius_policy=0) -> Handle:
+             k_target=40, max_passes=1000, face_pool=24, stream=None, radius_policy=0, threads_per_cell=0) -> Handle:
     """Voronoi cells of all particles; ``pos`` is a CUDA [N,3] float32/float64 tensor."""
     import torch
 
@@ -186,7 +187,7 @@ def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), per
     pos = pos.contiguous()
     if mass is not None:
         mass = mass.to(device=pos.device, dtype=pos.dtype).contiguous()
-    p = _params(precision, k_target, max_passes, face_pool, radius_policy)
+    p = _params(precision, k_target, max_passes, face_pool, radius_policy, threads_per_cell)
     lo = (ctypes.c_double * 3)(*[float(v) for v in (box_lo if hasattr(box_lo, "__len__") else (box_lo,) * 3)])
     hi = (ctypes.c_double * 3)(*[float(v) for v in (box_hi if hasattr(box_hi, "__len__") else (box_hi,) * 3)])
     h = ctypes.c_void_p()
@@ -201,7 +202,7 @@ def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), per
     return Handle(h, pos.shape[0], pos.dtype, pos.device, stream)
 
 
-def _params(precision, k_target, max_passes, face_pool, radius_policy) -> vt_params:
+def _params(precision, k_target, max_passes, face_pool, radius_policy, threads_per_cell=0) -> vt_params:
     p = vt_default_params()
     p.precision = {"filter32": VT_FILTER32, "plain64": VT_PLAIN64}[precision] if isinstance(precision, str) \
         else int(precision)
@@ -209,11 +210,12 @@ def _params(precision, k_target, max_passes, face_pool, radius_policy) -> vt_par
     p.max_passes = int(max_passes)
     p.face_pool = int(face_pool)
     p.reserved[0] = int(radius_policy)
+    p.threads_per_cell = int(threads_per_cell)
     return p
 
 
 def vt_build_batched(pos, set_off, boxes, mass=None, precision="filter32", k_target=40, max_passes=1000,
-                     face_pool=24, stream=None, radius_policy=0) -> Handle:
+                     face_pool=24, stream=None, radius_policy=0, threads_per_cell=0) -> Handle:
     """Voronoi cells of independent bounded sets: ``pos`` a CUDA [N,3] tensor, set s the rows
     [set_off[s], set_off[s+1]) inside ``boxes[s] = (lo x, lo y, lo z, hi x, hi y, hi z)``."""
     import numpy as np
@@ -232,7 +234,7 @@ def vt_build_batched(pos, set_off, boxes, mass=None, precision="filter32", k_tar
     n_sets = len(off) - 1
     if n_sets < 1 or bx.shape[0] != n_sets or off[-1] != pos.shape[0]:
         raise VTError(VT_ERR_INVALID, "vt_build_batched: set_off / boxes / pos sizes disagree")
-    p = _params(precision, k_target, max_passes, face_pool, radius_policy)
+    p = _params(precision, k_target, max_passes, face_pool, radius_policy, threads_per_cell)
     h = ctypes.c_void_p()
     dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
     with torch.cuda.device(pos.device):

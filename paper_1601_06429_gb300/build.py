@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvt_gb300.so")
 SOURCES = ["vt_api.cu", "vt_sort.cu", "vt_post.cu", "vt_clip_f32.cu", "vt_clip_f64.cu", "vt_clip_exact.cu",
-           "vt_noalloc.cu"]
+           "vt_clip_thread.cu", "vt_noalloc.cu"]
 HEADERS = ["vt_internal.cuh", "vt_kernels.cuh", "vt_clip_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -41,7 +41,7 @@ void free_handle(vt_handle h) {
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     void* ptrs[] = {h->spos, h->perm, h->inv, h->tree_mem, h->cell, h->face_start, h->face_count, h->cstat,
                     h->exact_list, h->dens_sorted, h->faces, h->xws, h->tmp, h->nbr_off_cache, h->dstat,
-                    h->keys, h->keys_alt, h->vals_alt, h->cnt_in, h->sset, h->sgeo, h->soff, h->set_in};
+                    h->keys, h->keys_alt, h->vals_alt, h->cnt_in, h->sset, h->sgeo, h->soff, h->set_in, h->warp_list};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -75,6 +75,7 @@ ClipArgs clip_args(vt_handle h) {
     a.sset = h->sset;
     a.sgeo = h->sgeo;
     a.soff = h->soff;
+    a.warp_list = h->prm.threads_per_cell == 1 ? h->warp_list : nullptr;
     return a;
 }
 
@@ -152,7 +153,9 @@ int check_params(const vt_params* p, vt_params& prm) {
     vt_default_params(&prm);
     if (p) prm = *p;
     if (prm.precision != VT_PLAIN64 && prm.precision != VT_FILTER32) return VT_ERR_INVALID;
-    if (prm.reserved[0] < 0 || prm.reserved[0] > 1) return VT_ERR_INVALID;
+    if (prm.reserved[0] < 0 || prm.reserved[0] > 1 || prm.reserved[1] || prm.reserved[2]) return VT_ERR_INVALID;
+    if (prm.threads_per_cell == 0) prm.threads_per_cell = 32;
+    if (prm.threads_per_cell != 1 && prm.threads_per_cell != 32) return VT_ERR_INVALID;
     if (prm.k_target < 8 || prm.k_target > 120 || prm.max_passes < 1 || prm.max_passes > 100000 || prm.face_pool < 1 ||
         prm.face_pool > 128)
         return VT_ERR_INVALID;
@@ -234,6 +237,7 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
     h->cnt_in = A.get<uint16_t>(N);
     h->cstat = A.get<uint8_t>(N);
     h->exact_list = A.get<uint32_t>(N);
+    h->warp_list = A.get<uint32_t>(N);
     h->dens_sorted = A.get<double>(N);
     h->face_cap = (uint64_t)N * prm.face_pool;
     h->faces = A.get<Face>(h->face_cap);
@@ -456,6 +460,8 @@ int vt_status(vt_handle h, vt_stats* out) {
     out->reserved[0] = d.error_detail;
     out->reserved[1] = (int64_t)d.n_collect;
     out->reserved[2] = (int64_t)d.n_collected;
+    out->n_handed_over = (int64_t)d.n_warp_cells;
+    out->n_bucket_passes = (int64_t)d.n_bucket_passes;
     out->error_particle = -1;
     if (d.error && d.error_cell >= 0 && d.error_cell < h->N) {
         uint32_t pi = 0;

@@ -1445,10 +1445,12 @@ __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
         const unsigned chunk = EXACT ? 1u : (unsigned)CHUNK;
         if (lane == 0) base = atomicAdd(EXACT ? &A.st->work_next_exact : &A.st->work_next, chunk);
         base = __shfl_sync(0xffffffffu, base, 0);
-        uint32_t lim = EXACT ? *((volatile unsigned*)&A.st->n_exact_cells) : total;
+        const bool listed = !EXACT && A.warp_list != nullptr;
+        uint32_t lim = EXACT ? *((volatile unsigned*)&A.st->n_exact_cells)
+                             : listed ? *((volatile unsigned*)&A.st->n_warp_cells) : total;
         if (base >= lim) break;
         for (uint32_t q = base; q < base + chunk && q < lim; q++) {
-            uint32_t self = EXACT ? A.exact_list[q] : q;
+            uint32_t self = EXACT ? A.exact_list[q] : listed ? A.warp_list[q] : q;
             VT_T0(tall);
             int rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, !EXACT);
             if (rc == RC_RETRY_BOX) rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, false);

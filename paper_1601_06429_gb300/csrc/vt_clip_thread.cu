@@ -1,0 +1,849 @@
+// vt_clip_thread.cu -- the bulk clipping kernel: one thread per cell, one warp per bucket of 32 cells.
+//
+// The warp kernel (vt_clip_impl.cuh) spends a whole warp on one cell, and most of its instructions on
+// cross-lane steps (candidate search, ballots, shuffles).  Here the 32 cells of a tree bucket (32 consecutive
+// particles in Morton order, so neighbours in space) share one candidate search: the warp walks the tree once
+// per radius pass and streams the points near the bucket's box through shared memory in chunks; every lane then
+// clips its own cell against the chunk, in registers and its own local memory.  The clipping, the predicates
+// and the emitted records are those of the warp kernel:
+//   * the cell is the intersection of half-spaces n.y <= h (n = x_j - x_i, h = |n|^2/2), held as its dual
+//     triangulation (one triangle of plane ids per vertex, listed counter-clockwise seen from outside);
+//   * a vertex is strictly beyond a plane when n.v - h exceeds the forward error bound of make_vertex; an
+//     undecided test is redone in FP64 from the input coordinates (side64);
+//   * a plane at |n| >= 2R (R bounds the distance of every vertex) cannot cut, and a cell is final once every
+//     point closer than 2R has been examined (the security radius).
+// A cell this kernel cannot finish -- an FP64 test that stays undecided, an ill-conditioned vertex, a cell
+// larger than its capacities, a start box that was too small, a duplicate point, or a security radius beyond
+// the passes it makes -- goes to a list that the warp kernel then takes (and from there, if needed, the exact
+// kernel).  Every decision this kernel takes is certified, so both kernels produce the same cells.
+#include "vt_clip_impl.cuh"
+
+namespace vt {
+namespace {
+
+constexpr int TT = 64;        // triangles (cell vertices) per cell
+constexpr int TPL = 40;       // planes per cell: the six start walls and the cuts
+constexpr int TRM = 32;       // triangles removed by one cut
+constexpr int TCH = 256;      // points per chunk
+constexpr int TSTK = 256;     // traversal stack entries per warp
+constexpr int TWARPS = 4;     // warps per block
+constexpr int TPASSES = 6;    // radius passes per bucket
+constexpr int TMAXPTS = 16384;  // points streamed per bucket before the remaining cells are handed over
+
+// lane-local cell.  V: vertex (x, y, z) relative to the site and its error bound; Tr: three 8-bit plane ids;
+// Pl: plane (n, h); Pn: |n|; Ps / Pc: the plane's source (sorted index, or the bits of an artificial wall's h)
+// and code (periodic image 0..26, box wall 27+w, artificial wall 33+w).
+struct TCell {
+    float4 V[TT];
+    uint32_t Tr[TT];
+    float4 Pl[TPL];
+    float Pn[TPL];
+    uint32_t Ps[TPL];
+    uint8_t Pc[TPL];
+    int nT, nP;
+    float R2;          // >= the squared distance of every exact vertex
+    float bmin[3], bmax[3];
+};
+
+struct TSmem {
+    float4 chunk[TCH];     // x, y, z, sorted index (bits)
+    uint32_t key[TCH];     // distance-to-box-centre bits (low 8 bits cleared) | slot
+    uint32_t stack[TSTK];  // level << 27 | node
+};
+
+// local failure codes (the cell goes to the warp kernel)
+constexpr int TF_CAP = 1, TF_ILL = 2, TF_UNDECIDED = 3, TF_DUP = 4, TF_WALL = 5, TF_RADIUS = 6, TF_CAP_CUT = 7,
+              TF_CAP_PLANES = 8;
+
+__device__ __forceinline__ void tri_ids(uint32_t t, uint32_t& a, uint32_t& b, uint32_t& c) {
+    a = t & 255u; b = (t >> 8) & 255u; c = (t >> 16) & 255u;
+}
+
+__device__ __forceinline__ bool vertex_of(const TCell& C, uint32_t a, uint32_t b, uint32_t c, float4& v) {
+    const float4 A = C.Pl[a], B = C.Pl[b], Cc = C.Pl[c];
+    float vx, vy, vz, ev, rr;
+    make_vertex<float>(A.x, A.y, A.z, A.w, C.Pn[a], B.x, B.y, B.z, B.w, C.Pn[b], Cc.x, Cc.y, Cc.z, Cc.w, C.Pn[c],
+                       vx, vy, vz, ev, rr);
+    v = make_float4(vx, vy, vz, ev);
+    return ev < INFINITY;
+}
+
+// R2 and the outward-rounded box of the exact vertices
+__device__ void bound_cell(TCell& C) {
+    float r2 = 0.f, lo0 = 0.f, lo1 = 0.f, lo2 = 0.f, hi0 = 0.f, hi1 = 0.f, hi2 = 0.f;
+    for (int t = 0; t < C.nT; t++) {
+        const float4 v = C.V[t];
+        float r = __fadd_ru(__fsqrt_ru(__fmaf_ru(v.z, v.z, __fmaf_ru(v.y, v.y, __fmul_ru(v.x, v.x)))), v.w);
+        r2 = fmaxf(r2, __fmul_ru(r, r));
+        lo0 = fminf(lo0, __fsub_rd(v.x, v.w)); hi0 = fmaxf(hi0, __fadd_ru(v.x, v.w));
+        lo1 = fminf(lo1, __fsub_rd(v.y, v.w)); hi1 = fmaxf(hi1, __fadd_ru(v.y, v.w));
+        lo2 = fminf(lo2, __fsub_rd(v.z, v.w)); hi2 = fmaxf(hi2, __fadd_ru(v.z, v.w));
+    }
+    C.R2 = r2 * (1.f + 1e-6f);
+    C.bmin[0] = lo0; C.bmin[1] = lo1; C.bmin[2] = lo2;
+    C.bmax[0] = hi0; C.bmax[1] = hi1; C.bmax[2] = hi2;
+}
+
+// Start polytope: the box of half-side B around the site (artificial walls), cut by the real box walls when
+// the set is bounded and a wall is closer.  Returns 0 or a failure code.
+template <typename P>
+__device__ int init_cell(TCell& C, const Geometry& g, const P& pi, uint32_t self, float B) {
+    for (int w = 0; w < 6; w++) {
+        const int axis = w >> 1;
+        const bool upper = (w & 1) == 0;
+        const double xi = axis == 0 ? (double)pi.x : axis == 1 ? (double)pi.y : (double)pi.z;
+        const double real = upper ? g.hi[axis] - xi : xi - g.lo[axis];
+        const float sg = upper ? 1.f : -1.f;
+        float4 pl = make_float4(axis == 0 ? sg : 0.f, axis == 1 ? sg : 0.f, axis == 2 ? sg : 0.f, 0.f);
+        if (!g.periodic && real <= (double)B) {
+            pl.w = (float)real;
+            C.Ps[w] = self;
+            C.Pc[w] = (uint8_t)(CODE_WALL + w);
+        } else {
+            pl.w = B;
+            C.Ps[w] = __float_as_uint(B);
+            C.Pc[w] = (uint8_t)(CODE_ART + w);
+        }
+        C.Pl[w] = pl;
+        C.Pn[w] = 1.f;
+    }
+    C.nP = 6;
+    // corners: planes x upper 0 / lower 1, y 2/3, z 4/5, counter-clockwise seen from outside
+    for (int k = 0; k < 8; k++) {
+        const int sx = (k & 1) ? -1 : 1, sy = (k & 2) ? -1 : 1, sz = (k & 4) ? -1 : 1;
+        const uint32_t X = (k & 1) ? 1 : 0, Y = (k & 2) ? 3 : 2, Z = (k & 4) ? 5 : 4;
+        const uint32_t t = (sx * sy * sz > 0) ? (X | (Y << 8) | (Z << 16)) : (X | (Z << 8) | (Y << 16));
+        C.Tr[k] = t;
+        float4 v;
+        uint32_t a, b, c;
+        tri_ids(t, a, b, c);
+        if (!vertex_of(C, a, b, c, v)) return TF_ILL;
+        C.V[k] = v;
+    }
+    C.nT = 8;
+    bound_cell(C);
+    return 0;
+}
+
+// Drop plane ids that no triangle uses (the start walls keep theirs).  Returns false if none is free.
+__device__ bool compact_planes(TCell& C) {
+    uint64_t used = 0x3full;
+    for (int t = 0; t < C.nT; t++) {
+        uint32_t a, b, c;
+        tri_ids(C.Tr[t], a, b, c);
+        used |= (1ull << a) | (1ull << b) | (1ull << c);
+    }
+    uint8_t map[TPL];
+    int n = 0;
+    for (int p = 0; p < C.nP; p++) {
+        if ((used >> p) & 1ull) {
+            if (n != p) {
+                C.Pl[n] = C.Pl[p]; C.Pn[n] = C.Pn[p]; C.Ps[n] = C.Ps[p]; C.Pc[n] = C.Pc[p];
+            }
+            map[p] = (uint8_t)n++;
+        }
+    }
+    if (n == C.nP) return false;
+    for (int t = 0; t < C.nT; t++) {
+        uint32_t a, b, c;
+        tri_ids(C.Tr[t], a, b, c);
+        C.Tr[t] = (uint32_t)map[a] | ((uint32_t)map[b] << 8) | ((uint32_t)map[c] << 16);
+    }
+    C.nP = n;
+    return true;
+}
+
+// Cut by plane (n, h) known to remove exactly the triangles in bm[].  Every directed edge x->y of a removed
+// triangle whose reverse y->x is in no removed triangle lies on the boundary of the removed region (its
+// neighbour across is kept) and becomes the new triangle (x, y, p).  New triangles fill the removed slots; the
+// array is then compacted.  Returns 0 or a failure code.
+__device__ int cut_cell(TCell& C, const unsigned* bm, float nx, float ny, float nz, float h, float nrm, uint32_t src,
+                        int code) {
+    if (C.nP >= TPL && !compact_planes(C)) return TF_CAP_PLANES;
+    const uint32_t p = (uint32_t)C.nP++;
+    C.Pl[p] = make_float4(nx, ny, nz, h);
+    C.Pn[p] = nrm;
+    C.Ps[p] = src;
+    C.Pc[p] = (uint8_t)code;
+    uint8_t rem[TRM];
+    uint32_t rtri[TRM];
+    int r = 0;
+    for (int w = 0; w < TT / 32; w++) {
+        unsigned m = bm[w];
+        while (m) {
+            const int t = w * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            if (r == TRM) return TF_CAP_CUT;
+            rtri[r] = C.Tr[t];
+            rem[r++] = (uint8_t)t;
+        }
+    }
+    uint8_t bx[TRM + 2], by[TRM + 2];
+    int nb = 0;
+    for (int k = 0; k < r; k++) {
+        uint32_t id[3];
+        tri_ids(rtri[k], id[0], id[1], id[2]);
+        for (int e = 0; e < 3; e++) {
+            const uint32_t x = id[e], y = id[e == 2 ? 0 : e + 1];
+            bool inner = false;
+            for (int k2 = 0; k2 < r && !inner; k2++) {
+                if (k2 == k) continue;
+                uint32_t a, b, c;
+                tri_ids(rtri[k2], a, b, c);
+                inner = (a == y && b == x) || (b == y && c == x) || (c == y && a == x);
+            }
+            if (!inner) {
+                if (nb == TRM + 2) return TF_CAP_CUT;
+                bx[nb] = (uint8_t)x;
+                by[nb] = (uint8_t)y;
+                nb++;
+            }
+        }
+    }
+    if (nb < 3) return TF_CAP_CUT;
+    if (C.nT - r + nb > TT) return TF_CAP;
+    for (int i = 0; i < nb; i++) {
+        const int slot = i < r ? (int)rem[i] : C.nT + (i - r);
+        const uint32_t t = (uint32_t)bx[i] | ((uint32_t)by[i] << 8) | (p << 16);
+        float4 v;
+        if (!vertex_of(C, bx[i], by[i], p, v)) return TF_ILL;
+        C.Tr[slot] = t;
+        C.V[slot] = v;
+    }
+    if (nb >= r) {
+        C.nT += nb - r;
+    } else {
+        // holes rem[nb..r) (ascending): move the last live triangles into those below the new count
+        const int n2 = C.nT - (r - nb);
+        unsigned hm[TT / 32] = {0u, 0u};
+        for (int i = nb; i < r; i++) hm[rem[i] >> 5] |= 1u << (rem[i] & 31);
+        int top = C.nT - 1;
+        for (int i = nb; i < r; i++) {
+            const int hole = rem[i];
+            if (hole >= n2) break;
+            while (top >= n2 && ((hm[top >> 5] >> (top & 31)) & 1u)) top--;
+            C.Tr[hole] = C.Tr[top];
+            C.V[hole] = C.V[top];
+            top--;
+        }
+        C.nT = n2;
+    }
+    return 0;
+}
+
+// n.v - h against the error bound for every vertex: beyond -> bm, undecided -> um
+__device__ __forceinline__ void test_plane(const TCell& C, float nx, float ny, float nz, float h, float nrm, float hb,
+                                           unsigned* bm, unsigned* um) {
+    bm[0] = bm[1] = 0u;
+    um[0] = um[1] = 0u;
+    for (int t = 0; t < C.nT; t++) {
+        const float4 v = C.V[t];
+        const float s = __fmaf_rn(nx, v.x, __fmaf_rn(ny, v.y, __fmaf_rn(nz, v.z, -h)));
+        const float bound = __fmaf_rn(nrm, v.w, hb);
+        const unsigned bit = 1u << (t & 31);
+        if (s > bound) bm[t >> 5] |= bit;
+        else if (!(s < -bound)) um[t >> 5] |= bit;
+    }
+}
+
+// gap between [lo, hi] and [blo, bhi] along one axis (minimum image when periodic)
+__device__ __forceinline__ float iv_gap(float lo, float hi, float blo, float bhi, float L, int periodic) {
+    float d = fmaxf(fmaxf(lo - bhi, blo - hi), 0.f);
+    if (periodic) {
+        d = fminf(d, fmaxf(fmaxf(lo + L - bhi, blo - hi - L), 0.f));
+        d = fminf(d, fmaxf(fmaxf(lo - L - bhi, blo - hi + L), 0.f));
+    }
+    return d;
+}
+
+// Sort (key, val) across the warp by decreasing key (bitonic network over the lanes).
+__device__ __forceinline__ void warp_sort_desc(float& key, uint32_t& val) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            const float ok = __shfl_xor_sync(0xffffffffu, key, jj);
+            const uint32_t ov = __shfl_xor_sync(0xffffffffu, val, jj);
+            const bool down = ((lane & k) == 0);     // this half ends decreasing
+            const bool lower = (lane & jj) == 0;
+            const bool take_big = (lower == down);
+            const bool other_bigger = ok > key || (ok == key && ov < val);
+            if (take_big == other_bigger) { key = ok; val = ov; }
+        }
+}
+
+// Resume the warp's walk of the tree: points (sorted index in [ilo, ihi)) whose gap to the bucket box has
+// g2lo <= gap^2 < g2hi are appended to the chunk until fewer than 32 slots are free or the stack is empty.
+__device__ int walk(TSmem& S, int& sp, int cnt, const float4* spos4, const void* spos, bool f64, const Tree& t,
+                    const Geometry& g, const float* blo, const float* bhi, float g2lo, float g2hi, int64_t ilo,
+                    int64_t ihi, bool& stack_ovf) {
+    const unsigned lane = lane_id(), lt = lanemask_lt();
+    while (sp > 0 && cnt <= TCH - 32) {
+        const uint32_t ent = S.stack[sp - 1];
+        sp--;
+        __syncwarp();
+        const int lvl = (int)(ent >> 27);
+        const int64_t node = ent & ((1u << 27) - 1);
+        if (lvl == 1) {
+            const int64_t j = node * 32 + lane;
+            bool hit = false;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j >= ilo && j < ihi) {
+                if (f64) {
+                    const dpt4 d = ((const dpt4*)spos)[j];
+                    q = make_float4((float)d.x, (float)d.y, (float)d.z, 0.f);
+                } else {
+                    q = spos4[j];
+                }
+                const float dx = axis_gap(q.x, blo[0], bhi[0], g.Lf[0], g.periodic);
+                const float dy = axis_gap(q.y, blo[1], bhi[1], g.Lf[1], g.periodic);
+                const float dz = axis_gap(q.z, blo[2], bhi[2], g.Lf[2], g.periodic);
+                const float g2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+                hit = g2 >= g2lo && g2 < g2hi;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                q.w = __uint_as_float((uint32_t)j);
+                S.chunk[cnt + __popc(m & lt)] = q;
+            }
+            cnt += __popc(m);
+        } else {
+            const int cl = lvl - 1;
+            const int64_t c = node * 32 + lane;
+            const int64_t span = (int64_t)1 << (5 * cl);
+            bool hit = false;
+            float gap2 = -1.f;
+            if (c < t.count[cl] && c * span < ihi && (c + 1) * span > ilo) {
+                const float4 lo = t.lo[t.off[cl] + c], hi = t.hi[t.off[cl] + c];
+                const float dx = iv_gap(lo.x, hi.x, blo[0], bhi[0], g.Lf[0], g.periodic);
+                const float dy = iv_gap(lo.y, hi.y, blo[1], bhi[1], g.Lf[1], g.periodic);
+                const float dz = iv_gap(lo.z, hi.z, blo[2], bhi[2], g.Lf[2], g.periodic);
+                gap2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+                hit = gap2 < g2hi * 1.0001f + 1e-30f;
+            }
+            const int nh = __popc(__ballot_sync(0xffffffffu, hit));
+            if (sp + nh > TSTK) {
+                stack_ovf = true;
+                return cnt;
+            }
+            // nearest child on top of the stack: the points arrive roughly by distance from the bucket
+            float key = hit ? gap2 : -1.f;
+            uint32_t val = hit ? (((uint32_t)cl << 27) | (uint32_t)c) : 0xffffffffu;
+            warp_sort_desc(key, val);
+            if ((int)lane < nh) S.stack[sp + lane] = val;
+            sp += nh;
+            __syncwarp();
+        }
+    }
+    return cnt;
+}
+
+// bitonic sort of the chunk keys [0, n) padded to a power of two
+__device__ void sort_keys(TSmem& S, int n) {
+    const unsigned lane = lane_id();
+    int m = 32;
+    while (m < n) m <<= 1;
+    for (int k = n + (int)lane; k < m; k += 32) S.key[k] = 0xffffffffu;
+    __syncwarp();
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = (int)lane; i < m; i += 32) {
+                const int ixj = i ^ jj;
+                if (ixj > i) {
+                    const uint32_t a = S.key[i], b = S.key[ixj];
+                    const bool asc = (i & k) == 0;
+                    if ((a > b) == asc) { S.key[i] = b; S.key[ixj] = a; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+struct TCount {
+    unsigned long long tested, cut, fp64, passes, collected;
+};
+
+// Filter the chunk for one lane's cell, then test the survivors and cut (lanes in step).  The filter works on
+// a cheap displacement (one rounding per component, periodic shift by rint) and keeps a point unless it is
+// farther than 2R, or its plane misses the cell's box, by more than the margin `slack` covers.  Survivors are
+// taken in six distance classes (near2 x 1, 2, 4, 8, 16, more), nearest first; each is re-checked against the
+// shrunken cell with the exact displacement before its test.  Returns 0 or a failure code for the lane.
+template <typename P>
+__device__ int clip_chunk(const TSmem& S, int cnt, TCell& C, const P* spos, const Geometry& g, const P& pi,
+                          uint32_t self, int64_t slo, int64_t shi, bool active, float near2, float slack,
+                          TCount& tc) {
+    const float u = Prec<float>::u();
+    uint8_t pend[TCH];
+    int np = 0;
+    if (active) {
+        uint16_t lv[TCH];
+        int nl[6] = {0, 0, 0, 0, 0, 0};
+        const float qx = (float)pi.x, qy = (float)pi.y, qz = (float)pi.z;
+        const float iLx = 1.f / g.Lf[0], iLy = 1.f / g.Lf[1], iLz = 1.f / g.Lf[2];
+        const float bext = fmaxf(fmaxf(fmaxf(-C.bmin[0], C.bmax[0]), fmaxf(-C.bmin[1], C.bmax[1])),
+                                 fmaxf(-C.bmin[2], C.bmax[2]));
+        const float rad = 2.f * sqrtf(C.R2);
+        const float rskip = rad * (1.f + 1e-5f) + 4.f * slack;
+        const float rskip2 = rskip * rskip;
+        const float stol = 1e-5f * (4.f * bext * rad + rad * rad) + 8.f * slack * (bext + rad) + 1e-30f;
+        for (int k = 0; k < cnt; k++) {
+            const uint32_t e = S.key[k] & 255u;
+            const float4 q = S.chunk[e];
+            const uint32_t j = __float_as_uint(q.w);
+            float dx = q.x - qx, dy = q.y - qy, dz = q.z - qz;
+            if (g.periodic) {
+                dx -= g.Lf[0] * rintf(dx * iLx);
+                dy -= g.Lf[1] * rintf(dy * iLy);
+                dz -= g.Lf[2] * rintf(dz * iLz);
+            }
+            const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+            if (d2 > rskip2) continue;
+            if (j == self || (int64_t)j < slo || (int64_t)j >= shi) continue;
+            const float sg = supp_g(dx, C.bmin[0], C.bmax[0]) + supp_g(dy, C.bmin[1], C.bmax[1]) +
+                             supp_g(dz, C.bmin[2], C.bmax[2]);
+            if (sg < -stol) continue;
+            const int l = (d2 >= near2) + (d2 >= 2.f * near2) + (d2 >= 4.f * near2) + (d2 >= 8.f * near2) +
+                          (d2 >= 16.f * near2);
+            lv[np++] = (uint16_t)(e | (l << 8));
+            nl[l]++;
+        }
+        int o[6];
+        o[0] = 0;
+#pragma unroll
+        for (int l = 1; l < 6; l++) o[l] = o[l - 1] + nl[l - 1];
+        for (int k = 0; k < np; k++) {
+            const int l = lv[k] >> 8;
+            pend[o[l]++] = (uint8_t)(lv[k] & 255u);
+        }
+    }
+    int kmax = np;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    int fail = 0;
+    for (int k = 0; k < kmax; k++) {
+        if (!active || fail || k >= np) continue;
+        const float4 q = S.chunk[pend[k]];
+        const uint32_t j = __float_as_uint(q.w);
+        float dx, dy, dz;
+        int code;
+        DispF<P, float>::get(spos[j], pi, g, dx, dy, dz, code);
+        const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+        if (d2 == 0.f) { fail = TF_DUP; continue; }
+        if (d2 * (1.f - 8.f * u) > 4.f * C.R2) continue;
+        {
+            // the cell's box has shrunk since the filter
+            const float bext = fmaxf(fmaxf(fmaxf(-C.bmin[0], C.bmax[0]), fmaxf(-C.bmin[1], C.bmax[1])),
+                                     fmaxf(-C.bmin[2], C.bmax[2]));
+            const float rad2 = 4.f * C.R2;
+            const float stol = 1e-5f * (4.f * bext * sqrtf(rad2) + rad2) + 1e-30f;
+            const float sg = supp_g(dx, C.bmin[0], C.bmax[0]) + supp_g(dy, C.bmin[1], C.bmax[1]) +
+                             supp_g(dz, C.bmin[2], C.bmax[2]);
+            if (sg < -stol) continue;
+        }
+        const float h = 0.5f * d2;
+        const float nrm = sqrtf(d2);
+        const float hb = 16.f * u * h;
+        unsigned bm[TT / 32], um[TT / 32];
+        test_plane(C, dx, dy, dz, h, nrm, hb, bm, um);
+        tc.tested++;
+        // undecided vertices: FP64 from the inputs
+        for (int w = 0; w < TT / 32 && !fail; w++) {
+            unsigned m = um[w];
+            while (m) {
+                const int t = w * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                uint32_t a, b, c;
+                tri_ids(C.Tr[t], a, b, c);
+                const PRef ra = {C.Ps[a], C.Pc[a]}, rb = {C.Ps[b], C.Pc[b]}, rc = {C.Ps[c], C.Pc[c]};
+                const PRef rj = {j, (uint8_t)code};
+                const int sd = side64<P>(spos, g, self, ra, rb, rc, rj);
+                tc.fp64++;
+                if (sd == 0) { fail = TF_UNDECIDED; break; }
+                if (sd > 0) bm[w] |= 1u << (t & 31);
+            }
+        }
+        if (fail) continue;
+        if ((bm[0] | bm[1]) == 0u) continue;
+        fail = cut_cell(C, bm, dx, dy, dz, h, nrm, j, code);
+        if (fail) continue;
+        tc.cut++;
+        bound_cell(C);
+    }
+    return fail;
+}
+
+// Planes that carry a facet (appear in a triangle) and the number of facet records (planes between particles);
+// -1 when the cell touches an artificial wall (its start box was too small).
+__device__ int count_faces(const TCell& C, uint64_t* present) {
+    uint64_t pm = 0ull;
+    for (int t = 0; t < C.nT; t++) {
+        uint32_t a, b, c;
+        tri_ids(C.Tr[t], a, b, c);
+        pm |= (1ull << a) | (1ull << b) | (1ull << c);
+    }
+    int nf = 0;
+    for (int p = 0; p < C.nP; p++) {
+        if (!((pm >> p) & 1ull)) continue;
+        if (C.Pc[p] >= CODE_ART) return -1;
+        if (p >= 6 && C.Pc[p] < 27) nf++;
+    }
+    *present = pm;
+    return nf;
+}
+
+// Facets of a finished cell: per plane, its triangles walked around the plane (the successor of (p, q, r) is the
+// triangle (p, r, s)) and fanned from the first vertex, with the formulas of the warp kernel's emission; facet
+// records go to out[] in plane order.  Returns false if a facet cannot be walked or the volume is not positive.
+__device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& vol, float& mzx, float& mzy,
+                           float& mzz, float& m2) {
+    vol = mzx = mzy = mzz = m2 = 0.f;
+    int w = 0;
+    for (int p = 0; p < C.nP; p++) {
+        if (!((present >> p) & 1ull)) continue;
+        uint8_t ft[32], fq[32], fr[32];
+        int m = 0;
+        for (int t = 0; t < C.nT; t++) {
+            uint32_t a, b, c;
+            tri_ids(C.Tr[t], a, b, c);
+            uint32_t q, r;
+            if (a == (uint32_t)p) { q = b; r = c; }
+            else if (b == (uint32_t)p) { q = c; r = a; }
+            else if (c == (uint32_t)p) { q = a; r = b; }
+            else continue;
+            if (m == 32) return false;
+            ft[m] = (uint8_t)t; fq[m] = (uint8_t)q; fr[m] = (uint8_t)r;
+            m++;
+        }
+        if (m < 3) return false;
+        const float4 v0 = C.V[ft[0]];
+        const float4 pl = C.Pl[p];
+        const float inrm = 1.f / C.Pn[p];
+        const float nhx = pl.x * inrm, nhy = pl.y * inrm, nhz = pl.z * inrm;
+        float A_ = 0.f, csx = 0.f, csy = 0.f, csz = 0.f, sm2 = 0.f;
+        int cur = -1, steps = 1;
+        for (int k = 1; k < m; k++)
+            if (fq[k] == fr[0]) { cur = k; break; }
+        for (int guard = 0; guard < m && cur > 0; guard++) {
+            int nxt = -1;
+            for (int k = 0; k < m; k++)
+                if (fq[k] == fr[cur]) { nxt = k; break; }
+            steps++;
+            if (nxt <= 0) break;
+            const float4 v1 = C.V[ft[cur]], v2 = C.V[ft[nxt]];
+            const float e1x = v1.x - v0.x, e1y = v1.y - v0.y, e1z = v1.z - v0.z;
+            const float e2x = v2.x - v0.x, e2y = v2.y - v0.y, e2z = v2.z - v0.z;
+            const float crx = __fmaf_rn(e1y, e2z, -e1z * e2y), cry = __fmaf_rn(e1z, e2x, -e1x * e2z),
+                        crz = __fmaf_rn(e1x, e2y, -e1y * e2x);
+            const float at = 0.5f * __fmaf_rn(crx, nhx, __fmaf_rn(cry, nhy, crz * nhz));
+            A_ += at;
+            const float third = (float)(1.0 / 3.0);
+            csx = __fmaf_rn(at * third, v0.x + v1.x + v2.x, csx);
+            csy = __fmaf_rn(at * third, v0.y + v1.y + v2.y, csy);
+            csz = __fmaf_rn(at * third, v0.z + v1.z + v2.z, csz);
+            float s2 = __fmaf_rn(v0.x, v0.x + v1.x + v2.x, __fmaf_rn(v0.y, v0.y + v1.y + v2.y, v0.z * (v0.z + v1.z + v2.z)));
+            s2 = __fmaf_rn(v1.x, v1.x + v2.x, __fmaf_rn(v1.y, v1.y + v2.y, __fmaf_rn(v1.z, v1.z + v2.z, s2)));
+            s2 = __fmaf_rn(v2.x, v2.x, __fmaf_rn(v2.y, v2.y, __fmaf_rn(v2.z, v2.z, s2)));
+            sm2 = __fmaf_rn(at, s2, sm2);
+            cur = nxt;
+        }
+        if (steps != m) return false;  // the walk did not close over all of the plane's triangles
+        const float dist = pl.w * inrm;
+        vol += dist * A_ * (float)(1.0 / 3.0);
+        mzx += dist * csx * 0.25f;
+        mzy += dist * csy * 0.25f;
+        mzz += dist * csz * 0.25f;
+        m2 += dist * sm2 * (float)(1.0 / 30.0);
+        if (p >= 6 && C.Pc[p] < 27) {
+            Face f;
+            f.dx = pl.x; f.dy = pl.y; f.dz = pl.z;
+            f.area = A_;
+            if (A_ != 0.f) { f.cx = csx / A_; f.cy = csy / A_; f.cz = csz / A_; }
+            else { f.cx = f.cy = f.cz = 0.f; }
+            f.nbr = C.Ps[p];
+            out[w++] = f;
+        }
+    }
+    return vol > 0.f;
+}
+
+template <typename P>
+__global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
+    __shared__ TSmem smem[TWARPS];
+    TSmem& S = smem[threadIdx.x >> 5];
+    const unsigned lane = lane_id(), lt = lanemask_lt();
+    if (*((volatile unsigned*)&A.st->invalid_input)) return;
+    const P* spos = (const P*)A.spos;
+    const bool f64 = sizeof(P) != 16;
+    const float u = Prec<float>::u();
+    const int64_t nbuckets = (A.N + 31) / 32;
+    TCount tc = {0ull, 0ull, 0ull, 0ull, 0ull};
+    TCell C;
+    for (;;) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(&A.st->work_next_bucket, 1ull);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if ((int64_t)b >= nbuckets) break;
+        const int64_t self64 = (int64_t)b * 32 + lane;
+        const bool alive = self64 < A.N;
+        const uint32_t self = alive ? (uint32_t)self64 : 0u;
+        Geometry g = A.geo;
+        int64_t slo = 0, shi = A.N;
+        if (A.sset && alive) {
+            const uint32_t s = A.sset[self];
+            g = A.sgeo[s];
+            slo = A.soff[s];
+            shi = A.soff[s + 1];
+        }
+        const P pi = spos[self];
+        const float qx = (float)pi.x, qy = (float)pi.y, qz = (float)pi.z;
+        // the bucket's box (over its live cells) and index range
+        float blo[3] = {alive ? qx : INFINITY, alive ? qy : INFINITY, alive ? qz : INFINITY};
+        float bhi[3] = {alive ? qx : -INFINITY, alive ? qy : -INFINITY, alive ? qz : -INFINITY};
+        int64_t ilo = alive ? slo : INT64_MAX, ihi = alive ? shi : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                blo[a] = fminf(blo[a], __shfl_xor_sync(0xffffffffu, blo[a], o));
+                bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(0xffffffffu, bhi[a], o));
+            }
+            ilo = min(ilo, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)ilo, o));
+            ihi = max(ihi, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)ihi, o));
+        }
+        // first radius: 1.6 x the median over the lanes of the distance to the 4th nearest bucket mate (about the
+        // reach of a cell's facets; later passes widen it to what the unfinished cells need)
+        float d4, near2;
+        {
+            float k0 = INFINITY, k1 = INFINITY, k2 = INFINITY, k3 = INFINITY;
+            for (int l = 0; l < 32; l++) {
+                const float ox = __shfl_sync(0xffffffffu, qx, l), oy = __shfl_sync(0xffffffffu, qy, l),
+                            oz = __shfl_sync(0xffffffffu, qz, l);
+                const int oi = __shfl_sync(0xffffffffu, (int)alive, l);
+                const int64_t ol = (int64_t)b * 32 + l;
+                if (!oi || l == (int)lane || ol < slo || ol >= shi) continue;
+                float dx = fabsf(ox - qx), dy = fabsf(oy - qy), dz = fabsf(oz - qz);
+                if (g.periodic) {
+                    dx = fminf(dx, g.Lf[0] - dx); dy = fminf(dy, g.Lf[1] - dy); dz = fminf(dz, g.Lf[2] - dz);
+                }
+                float d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 < k3) {
+                    if (d2 < k2) { k3 = k2; if (d2 < k1) { k2 = k1; if (d2 < k0) { k1 = k0; k0 = d2; } else k1 = d2; } else k2 = d2; }
+                    else k3 = d2;
+                }
+            }
+            d4 = alive ? k3 : INFINITY;
+            near2 = k3;
+            // median over the lanes (infinite values sort last)
+            for (int k = 2; k <= 32; k <<= 1)
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    const float o = __shfl_xor_sync(0xffffffffu, d4, jj);
+                    const bool up = ((lane & k) == 0), lower = (lane & jj) == 0;
+                    const float mn = fminf(d4, o), mx = fmaxf(d4, o);
+                    d4 = (lower == up) ? mn : mx;
+                }
+            const int n_alive = __popc(__ballot_sync(0xffffffffu, alive));
+            d4 = __shfl_sync(0xffffffffu, d4, n_alive / 2);
+        }
+        const double lmin = fmin(g.L[0], fmin(g.L[1], g.L[2]));
+        float rho;
+        if (d4 < INFINITY && d4 > 0.f) rho = 1.6f * sqrtf(d4);
+        else rho = (float)(2.0 * cbrt(g.L[0] * g.L[1] * g.L[2] / (double)max((int64_t)1, shi - slo)));
+        rho = __shfl_sync(0xffffffffu, rho, 0);  // lanes of one bucket share the radius
+        const float rho_cap = g.periodic ? (float)(0.24 * lmin) : INFINITY;
+        if (rho > rho_cap) rho = rho_cap;
+        if (!(near2 < INFINITY) || near2 <= 0.f) near2 = rho * rho * (1.f / 16.f);
+        // rounding of the gaps (coordinates, box ends and periodic shifts carry a few ulps of the box scale);
+        // the same for every lane of the bucket
+        float slack = 16.f * u * fmaxf(fmaxf(fmaxf(fabsf(g.hif[0]), fabsf(g.lof[0])), fmaxf(fabsf(g.hif[1]), fabsf(g.lof[1]))),
+                                        fmaxf(fmaxf(fabsf(g.hif[2]), fabsf(g.lof[2])), fmaxf(g.Lf[0], fmaxf(g.Lf[1], g.Lf[2])))) + 1e-30f;
+        slack = warp_max<float>(alive ? slack : 0.f);
+        int fail = 0;
+        // start box on the scale of the lane's own neighbourhood (a box that proves too small sends the cell to
+        // the warp kernel)
+        const float Bown = fminf(4.f * rho, 3.f * sqrtf(near2));
+        if (alive) fail = init_cell<P>(C, g, pi, self, Bown);
+        bool done = !alive;
+        float g2prev = -1.f;
+        int streamed = 0;
+        for (int pass = 0; pass < TPASSES; pass++) {
+            const bool want = alive && !done && !fail;
+            if (!__any_sync(0xffffffffu, want)) break;
+            if (lane == 0) tc.passes++;
+            const float gr = rho * (1.f + 4.f * u) + slack;
+            const float g2hi = gr * gr * (1.f + 4.f * u);
+            // top level into the stack
+            int sp = 0;
+            {
+                const Tree& t = A.tree;
+                const int top = t.levels;
+                const int64_t span = (int64_t)1 << (5 * top);
+                bool hit = false;
+                if ((int64_t)lane < t.count[top] && lane * span < ihi && (lane + 1) * span > ilo) {
+                    const float4 lo = t.lo[t.off[top] + lane], hi = t.hi[t.off[top] + lane];
+                    const float dx = iv_gap(lo.x, hi.x, blo[0], bhi[0], g.Lf[0], g.periodic);
+                    const float dy = iv_gap(lo.y, hi.y, blo[1], bhi[1], g.Lf[1], g.periodic);
+                    const float dz = iv_gap(lo.z, hi.z, blo[2], bhi[2], g.Lf[2], g.periodic);
+                    hit = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx)) < g2hi * 1.0001f + 1e-30f;
+                }
+                float gap2 = -1.f;
+                if (hit) {
+                    const float4 lo = t.lo[t.off[top] + lane], hi = t.hi[t.off[top] + lane];
+                    const float dx = iv_gap(lo.x, hi.x, blo[0], bhi[0], g.Lf[0], g.periodic);
+                    const float dy = iv_gap(lo.y, hi.y, blo[1], bhi[1], g.Lf[1], g.periodic);
+                    const float dz = iv_gap(lo.z, hi.z, blo[2], bhi[2], g.Lf[2], g.periodic);
+                    gap2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+                }
+                const int nh = __popc(__ballot_sync(0xffffffffu, hit));
+                uint32_t val = hit ? (((uint32_t)top << 27) | lane) : 0xffffffffu;
+                warp_sort_desc(gap2, val);
+                if ((int)lane < nh) S.stack[lane] = val;
+                sp = nh;
+                __syncwarp();
+            }
+            bool ovf = false;
+            while (sp > 0) {
+                const int cnt = walk(S, sp, 0, (const float4*)A.spos, A.spos, f64, A.tree, g, blo, bhi, g2prev, g2hi,
+                                     ilo, ihi, ovf);
+                streamed += cnt;
+                if (lane == 0) tc.collected += cnt;
+                if (ovf || streamed > TMAXPTS) { ovf = true; break; }
+                if (cnt == 0) continue;
+                // nearest first (to the bucket's box centre)
+                {
+                    const float cx = 0.5f * (blo[0] + bhi[0]), cy = 0.5f * (blo[1] + bhi[1]), cz = 0.5f * (blo[2] + bhi[2]);
+                    for (int k = (int)lane; k < cnt; k += 32) {
+                        const float4 q = S.chunk[k];
+                        float dx = fabsf(q.x - cx), dy = fabsf(q.y - cy), dz = fabsf(q.z - cz);
+                        if (g.periodic) {
+                            dx = fminf(dx, g.Lf[0] - dx); dy = fminf(dy, g.Lf[1] - dy); dz = fminf(dz, g.Lf[2] - dz);
+                        }
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        S.key[k] = (__float_as_uint(d2) & ~255u) | (uint32_t)k;
+                    }
+                    __syncwarp();
+                    sort_keys(S, cnt);
+                }
+                const bool act = alive && !done && !fail;
+                const int f = clip_chunk<P>(S, cnt, C, spos, g, pi, self, slo, shi, act, near2, slack, tc);
+                if (act && f) fail = f;
+                __syncwarp();
+            }
+            if (ovf) {
+                if (alive && !done && !fail) fail = TF_RADIUS;
+                break;
+            }
+            g2prev = g2hi;
+            // certified: every point within rho of the site has been examined
+            if (alive && !done && !fail && 4.f * C.R2 <= rho * rho * (1.f - 8.f * u)) done = true;
+            // next radius: what the unfinished cells need, between 1.25 and 2 times the current one
+            float need = (alive && !done && !fail) ? 2.f * sqrtf(C.R2) * 1.001f : 0.f;
+            need = warp_max<float>(need);
+            if (need == 0.f) break;
+            float nxt = fminf(fmaxf(need, 1.25f * rho), 2.f * rho);
+            if (rho >= rho_cap) break;
+            rho = fminf(nxt, rho_cap);
+        }
+        if (alive && !done && !fail) fail = TF_RADIUS;
+        // ---------------- emission
+        int nf = 0;
+        uint64_t present = 0ull;
+        if (alive && !fail) {
+            nf = count_faces(C, &present);
+            if (nf < 0) fail = TF_WALL;
+        }
+        if (!(alive && !fail)) nf = 0;
+        // reserve the warp's facet records at once
+        int incl = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0ull;
+        if (lane == 0 && total > 0) base = atomicAdd(&A.st->face_next, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const bool pool_ok = base + (unsigned long long)total <= A.face_cap;
+        if (!pool_ok) {
+            if (lane == 0) atomicCAS(&A.st->error, 0, RC_POOL);
+            if (alive && !fail) fail = TF_CAP;
+        } else if (alive && !fail) {
+            const uint32_t start = (uint32_t)(base + (unsigned long long)(incl - nf));
+            float vol, mzx, mzy, mzz, m2;
+            if (!emit_faces(C, present, A.faces + start, vol, mzx, mzy, mzz, m2)) {
+                fail = TF_CAP_PLANES;  // its records are left unused; the warp kernel writes new ones
+            } else {
+                CellOut co;
+                co.vol = (double)vol;
+                co.zx = mzx / vol;
+                co.zy = mzy / vol;
+                co.zz = mzz / vol;
+                co.mom2 = m2;
+                A.cell[self] = co;
+                A.face_start[self] = start;
+                A.face_count[self] = (uint16_t)nf;
+                A.cstat[self] = CS_DONE;
+                atomicMax(&A.st->max_faces, (unsigned)nf);
+            }
+        }
+        const bool emit = alive && !fail;
+        // hand the unfinished cells to the warp kernel
+        const bool hand = alive && !emit;
+        if (hand) atomicAdd(&A.st->n_tfail[fail > 0 && fail < 8 ? fail : 0], 1ull);  // 0: plane capacity
+        const unsigned hm = __ballot_sync(0xffffffffu, hand);
+        if (hm) {
+            unsigned slot0 = 0;
+            if (lane == 0) slot0 = atomicAdd(&A.st->n_warp_cells, (unsigned)__popc(hm));
+            slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+            if (hand) A.warp_list[slot0 + __popc(hm & lt)] = self;
+        }
+        // facet records of the cells finished here
+        int nfe = emit ? nf : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nfe += __shfl_xor_sync(0xffffffffu, nfe, o);
+        if (lane == 0 && nfe > 0) atomicAdd(&A.st->n_faces, (unsigned long long)nfe);
+    }
+    // counters
+    unsigned long long v[5] = {tc.tested, tc.cut, tc.fp64, tc.passes, tc.collected};
+#pragma unroll
+    for (int k = 0; k < 5; k++)
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0) {
+        atomicAdd(&A.st->n_tested, v[0]);
+        atomicAdd(&A.st->n_cut, v[1]);
+        atomicAdd(&A.st->n_fp64, v[2]);
+        atomicAdd(&A.st->n_t_tested, v[0]);
+        atomicAdd(&A.st->n_t_cut, v[1]);
+        atomicAdd(&A.st->n_t_fp64, v[2]);
+        atomicAdd(&A.st->n_t_collected, v[4]);
+        atomicAdd(&A.st->n_bucket_passes, v[3]);
+        atomicAdd(&A.st->n_collected, v[4]);
+    }
+}
+
+}  // namespace
+
+int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s) {
+    static int per_sm_dev[2][64] = {{0}};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int k = dtype == VT_F32 ? 0 : 1;
+    int per_sm = (dev >= 0 && dev < 64) ? per_sm_dev[k][dev] : 0;
+    if (per_sm == 0) {
+        if (dtype == VT_F32)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip_thread<float4>, TWARPS * 32, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip_thread<dpt4>, TWARPS * 32, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (dev >= 0 && dev < 64) per_sm_dev[k][dev] = per_sm;
+    }
+    const int blocks = sm_count * per_sm;
+    if (dtype == VT_F32) k_clip_thread<float4><<<blocks, TWARPS * 32, 0, s>>>(a);
+    else k_clip_thread<dpt4><<<blocks, TWARPS * 32, 0, s>>>(a);
+    return 1;
+}
+
+}  // namespace vt

@@ -40,6 +40,12 @@ struct DevStatus {
     unsigned int invalid_input;      // count of NaN / out-of-box coordinates
     int error_detail;                // internal reason of the first error (capacity: -101 planes, -102 triangles,
                                      // -103 boundary, -104 candidates, -105 search stack)
+    unsigned long long work_next_bucket;  // bucket scheduler of the thread-per-cell kernel
+    unsigned long long n_bucket_passes;   // its radius passes (per bucket)
+    unsigned int n_warp_cells;            // cells it handed to the warp kernel (length of warp_list)
+    unsigned long long n_tfail[8];        // ... by reason (capacity, ill-conditioned vertex, undecided in FP64,
+                                          // duplicate, start box too small, security radius not reached)
+    unsigned long long n_t_tested, n_t_cut, n_t_fp64, n_t_collected;  // its own counters
 };
 
 // facet record (one per cell side of a facet between two particles)
@@ -100,6 +106,7 @@ struct vt_handle_s {
     uint16_t* face_count;   // [N] sorted order
     uint8_t* cstat;         // [N] sorted order
     uint32_t* exact_list;   // [N]
+    uint32_t* warp_list;    // [N] cells the thread-per-cell kernel hands to the warp kernel
     double* dens_sorted;    // [N] sorted order
     int dens_ready;
     uint64_t* keys;         // [N] Morton keys (sort)

@@ -53,9 +53,13 @@ struct ClipArgs {
     const uint32_t* sset;
     const Geometry* sgeo;
     const int64_t* soff;
+    // FP32 filter: the thread-per-cell kernel runs first and lists here (N entries) the cells the warp kernel
+    // must take; NULL: the warp kernel takes every cell
+    uint32_t* warp_list;
 };
 int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s);
 int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
+int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
 size_t exact_ws_doubles_per_warp();
 
 // post-processing (vt_post.cu)

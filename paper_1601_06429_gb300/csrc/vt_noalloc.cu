@@ -44,7 +44,7 @@ constexpr size_t kFaces = align256((size_t)kMaxN * kFacePool * sizeof(vt::Face))
 constexpr size_t kXws = align256((size_t)kExactWarps * 12288 * 8);
 constexpr size_t kTmp = align256(64 * 1024);
 constexpr size_t kStat = align256(sizeof(vt::DevStatus));
-constexpr size_t kTotal = kSpos + 2 * kKeys + 4 * kU32 + kU16 + kU8 + kTree + kCell + kFaces + kXws + kTmp + kStat;
+constexpr size_t kTotal = kSpos + 2 * kKeys + 5 * kU32 + kU16 + kU8 + kTree + kCell + kFaces + kXws + kTmp + kStat;
 
 __device__ __align__(256) unsigned char g_scratch[kTotal];
 
@@ -116,6 +116,7 @@ extern "C" int vt_volumes_noalloc(const void* pos, int dtype, int64_t N, const d
     uint32_t* vals_alt = (uint32_t*)q; q += kU32;
     uint32_t* inv = (uint32_t*)q; q += kU32;
     uint32_t* face_start = (uint32_t*)q; q += kU32;
+    uint32_t* warp_list = (uint32_t*)q; q += kU32;
     uint16_t* face_count = (uint16_t*)q; q += kU16;
     uint8_t* cstat = (uint8_t*)q; q += kU8;
     float4* tree_mem = (float4*)q; q += kTree;
@@ -158,6 +159,7 @@ extern "C" int vt_volumes_noalloc(const void* pos, int dtype, int64_t N, const d
     a.st = dstat;
     a.xws = xws;
     a.xws_warps = kExactWarps;
+    a.warp_list = warp_list;
     launch_clip(a, dtype, VT_FILTER32, sms, s);
     launch_clip_exact(a, dtype, sms, s);
     rc = rc_of(cudaGetLastError());

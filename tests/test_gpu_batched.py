@@ -30,9 +30,9 @@ def unit_boxes(n_sets):
     return np.tile(np.array([-1.0, -1.0, -1.0, 1.0, 1.0, 1.0]), (n_sets, 1))
 
 
-def run_batched(pts, off, boxes, precision="filter32"):
+def run_batched(pts, off, boxes, precision="filter32", threads_per_cell=0):
     pos = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
-    h = vt.vt_build_batched(pos, off, boxes, precision=precision)
+    h = vt.vt_build_batched(pos, off, boxes, precision=precision, threads_per_cell=threads_per_cell)
     vol, noff, ids = vt.cells(h)
     return h, vol.double().cpu().numpy(), noff.cpu().numpy(), ids.cpu().numpy()
 
@@ -60,11 +60,11 @@ def sets64():
     return inputs.halo_sets(n_sets=64, nmin=64, nmax=4096, seed=6, dtype=np.float32)
 
 
-@pytest.mark.parametrize("precision,tol", [("filter32", 2e-5), ("plain64", 1e-6)])
-def test_batched_matches_oracle_every_set(sets64, oracle_mod, precision, tol):
+@pytest.mark.parametrize("precision,tol,tpc", [("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("plain64", 1e-6, 32)])
+def test_batched_matches_oracle_every_set(sets64, oracle_mod, precision, tol, tpc):
     pts, off = sets64
     boxes = unit_boxes(len(off) - 1)
-    h, vol, noff, ids = run_batched(pts, off, boxes, precision)
+    h, vol, noff, ids = run_batched(pts, off, boxes, precision, tpc)
     for s in range(len(off) - 1):
         check_set(s, off, boxes[s], vol, noff, ids, pts, oracle_mod, tol)
     st = vt.vt_status(h)
@@ -124,8 +124,8 @@ def test_batched_varied_boxes_and_degenerate_sets(oracle_mod):
     pts = np.concatenate(parts)
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     boxes = np.array(boxes)
-    for precision, tol in (("plain64", 1e-6), ("filter32", 2e-5)):
-        h, vol, noff, ids = run_batched(pts, off, boxes, precision)
+    for precision, tol, tpc in (("plain64", 1e-6, 32), ("filter32", 2e-5, 32), ("filter32", 2e-5, 1)):
+        h, vol, noff, ids = run_batched(pts, off, boxes, precision, tpc)
         for s in range(len(sizes)):
             check_set(s, off, boxes[s], vol, noff, ids, pts, oracle_mod, tol)
         one = int(off[5])  # sets: 0, 1, empty, 2, 3, one point, 4, two points, 5

@@ -100,6 +100,17 @@ def test_uniform4096_filter32(uniform4096, oracle_mod):
     assert abs(g["vol"].sum() - 1.0) < 1e-6
 
 
+def test_uniform4096_thread_per_cell(uniform4096, oracle_mod):
+    """The thread-per-cell clipping kernel (cells it cannot finish go to the warp kernel) against the oracle."""
+    x, o = uniform4096
+    g = gpu_run(x, 0.0, 1.0, True, "filter32", threads_per_cell=1)
+    check_cells(g, o, oracle_mod, np.arange(len(x)), 2e-5)
+    assert abs(g["vol"].sum() - 1.0) < 1e-6
+    check_gradient(g, x, o, oracle_mod, np.arange(len(x)), 0.0, 1.0, 1e-1, 1e-4)
+    # it finishes nearly every cell of a uniform set itself
+    assert g["stats"]["n_handed_over"] <= 0.05 * len(x), g["stats"]["n_handed_over"]
+
+
 def test_uniform_fp32_inputs_both_precisions(oracle_mod):
     x = inputs.uniform(4096 + 7, seed=5, dtype=np.float32)  # ragged last bucket
     o = oracle_mod.cells(x.astype(np.float64), 0.0, 1.0, True, mode="certified")
@@ -139,10 +150,10 @@ def clustered64k(oracle_mod):
     return x, L, oracle_mod.cells(x.astype(np.float64), 0.0, L, True, mode="certified")
 
 
-@pytest.mark.parametrize("prec,tol", [("filter32", 2e-5), ("plain64", 1e-6)])
-def test_clustered64k_all_cells(clustered64k, oracle_mod, prec, tol):
+@pytest.mark.parametrize("prec,tol,tpc", [("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("plain64", 1e-6, 32)])
+def test_clustered64k_all_cells(clustered64k, oracle_mod, prec, tol, tpc):
     x, L, o = clustered64k
-    g = gpu_run(x, 0.0, L, True, prec)
+    g = gpu_run(x, 0.0, L, True, prec, threads_per_cell=tpc)
     check_cells(g, o, oracle_mod, np.arange(len(x)), tol)
     assert abs(g["vol"].sum() / L ** 3 - 1.0) < 1e-6
     floor = 1e-3 if prec == "plain64" else 1e-1
@@ -155,8 +166,8 @@ def test_bounded_halo_sets(oracle_mod):
     for s in range(3):
         x = pts[off[s]:off[s + 1]]
         o = oracle_mod.cells(x.astype(np.float64), -1.0, 1.0, False, mode="certified")
-        for prec, tol in (("filter32", 2e-5), ("plain64", 1e-6)):
-            g = gpu_run(x, -1.0, 1.0, False, prec)
+        for prec, tol, tpc in (("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("plain64", 1e-6, 32)):
+            g = gpu_run(x, -1.0, 1.0, False, prec, threads_per_cell=tpc)
             check_cells(g, o, oracle_mod, np.arange(len(x)), tol)
             assert abs(g["vol"].sum() - 8.0) < 8e-6
 
