@@ -277,6 +277,18 @@ def run_ours(args):
     box = ((0.0,) * 3, (L,) * 3)
     set_off = desc.get("set_off")
     boxes = None if set_off is None else np.tile([-1.0, -1.0, -1.0, 1.0, 1.0, 1.0], (len(set_off) - 1, 1))
+    set_k = set_tpc = None
+    tuned = None
+    if set_off is not None and not args.no_autotune:
+        # per size class: k_target and threads per cell from timed trial builds (untimed here)
+        t0 = time.perf_counter()
+        set_k, set_tpc = vt.vt_autotune_batched(torch.from_numpy(x).to(dev), set_off, boxes, precision=args.precision)
+        sizes = np.diff(set_off)
+        cls = np.floor(np.log2(np.maximum(sizes, 1))).astype(int)
+        tuned = {"seconds": time.perf_counter() - t0,
+                 "per_size_class": {"%d..%d" % (2 ** cc, 2 ** (cc + 1) - 1):
+                                    {"k_target": int(set_k[cls == cc][0]), "threads_per_cell": int(set_tpc[cls == cc][0])}
+                                    for cc in np.unique(cls)}}
     stream = torch.cuda.current_stream(dev)
     xd = torch.from_numpy(x).to(dev)
     w = torch.from_numpy(np.random.default_rng(4).random(N).astype(np.float32)).to(dev)  # dL/dV weights
@@ -294,7 +306,7 @@ def run_ours(args):
         if set_off is None:
             h = vt.vt_build(pos_dev, None, box[0], box[1], True, args.precision)
         else:
-            h = vt.vt_build_batched(pos_dev, set_off, boxes, precision=args.precision)
+            h = vt.vt_build_batched(pos_dev, set_off, boxes, precision=args.precision, set_k=set_k, set_tpc=set_tpc)
         nnz = vt.vt_cells(h)
         if nnz > ids.numel():
             ids = torch.empty(int(nnz * 1.2), dtype=torch.int32, device=dev)
@@ -405,6 +417,8 @@ def run_ours(args):
             "device_counters": {k: stats[-1][k] for k in ("n_cut", "n_tested", "n_passes", "n_fp64_fallbacks",
                                                           "n_exact_cells", "n_exact_preds", "max_faces",
                                                           "n_handed_over", "n_bucket_passes")}}
+    if tuned is not None:
+        line["config"]["autotune"] = tuned
     if set_off is not None and not args.no_loop_baseline:
         line["per_set_loop"] = per_set_loop(vt, x, set_off, args.precision, dev, stream, N)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -479,6 +493,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-loop-baseline", action="store_true", help="batched workloads: skip the per-set loop")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workloads: default k_target, one warp per cell")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

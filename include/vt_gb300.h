@@ -159,6 +159,9 @@ int vt_rebuild(vt_handle h, const void *pos, const void *mass);
  *   n_sets   1 .. VT_MAX_SETS
  *   boxes    host [n_sets][6]: lo x,y,z then hi x,y,z of each set's box; the
  *            cells of a set are clipped by its box walls (no periodic images)
+ *   set_k    host [n_sets] k_target of each set, or NULL (p's k_target)
+ *   set_tpc  host [n_sets] threads_per_cell of each set (1 or 32; 0 means 32),
+ *            or NULL (p's threads_per_cell); see vt_autotune_batched
  *   p, stream  as for vt_build
  * A particle's neighbours are particles of its own set only.  The handle
  * answers vt_cells, vt_density, vt_gradient, vt_moments, vt_backward and
@@ -167,7 +170,26 @@ int vt_rebuild(vt_handle h, const void *pos, const void *mass);
  * Errors: those of vt_build; VT_ERR_INVALID also for a bad set_off or box.
  */
 int vt_build_batched(vt_handle *h, const void *pos, int dtype, const void *mass, const int64_t *set_off,
-                     int n_sets, const double *boxes, const vt_params *p, void *stream);
+                     int n_sets, const double *boxes, const int32_t *set_k, const int32_t *set_tpc,
+                     const vt_params *p, void *stream);
+
+/*
+ * vt_autotune_batched -- per-set clipping parameters for vt_build_batched,
+ * chosen by timing (the paper has no counterpart: its parameters are set by
+ * hand).  Sets are grouped by size class [2^c, 2^(c+1)); for each class, whole
+ * sets spread evenly through it, about `sample` points in all (<= 0: 262144),
+ * are copied to a temporary device buffer and built as one batch for every
+ * k_target in {16, 24, 32, 48, 64} and (FP32 filter) threads_per_cell in
+ * {32, 1}; the configuration with the shortest clipping time (CUDA events)
+ * wins for every set of the class.
+ *   pos, dtype, set_off, n_sets, boxes, p, stream  as for vt_build_batched
+ *   k_out, tpc_out  host out [n_sets]: the chosen k_target and
+ *                   threads_per_cell of each set (empty sets: p's k_target, 32)
+ * Synchronises; allocates and frees device memory.  The choice only changes
+ * the speed: the cells do not depend on it.  Errors: those of vt_build_batched.
+ */
+int vt_autotune_batched(const void *pos, int dtype, const int64_t *set_off, int n_sets, const double *boxes,
+                        const vt_params *p, int64_t sample, int32_t *k_out, int32_t *tpc_out, void *stream);
 
 /*
  * vt_cells -- cell volumes and neighbour lists (Implementation section:

@@ -83,7 +83,12 @@ def load_library(path: str = LIB_PATH):
                              ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(vt_params), P]
     lib.vt_build.restype = i32
     lib.vt_build_batched.argtypes = [ctypes.POINTER(P), P, i32, P, ctypes.POINTER(i64), i32,
-                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(vt_params), P]
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(vt_params), P]
+    lib.vt_autotune_batched.argtypes = [P, i32, ctypes.POINTER(i64), i32, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(vt_params), i64, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), P]
+    lib.vt_autotune_batched.restype = i32
     lib.vt_build_batched.restype = i32
     lib.vt_rebuild.argtypes = [P, P, P]
     lib.vt_rebuild.restype = i32
@@ -214,8 +219,38 @@ def _params(precision, k_target, max_passes, face_pool, radius_policy, threads_p
     return p
 
 
+def _i32p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def vt_autotune_batched(pos, set_off, boxes, precision="filter32", sample=0, stream=None, **kw):
+    """Per-set (k_target, threads_per_cell) chosen by timing trial builds per size class; two int32 arrays."""
+    import numpy as np
+    import torch
+
+    lib = load_library()
+    if not (isinstance(pos, torch.Tensor) and pos.is_cuda and pos.dim() == 2 and pos.shape[1] == 3
+            and pos.dtype in (torch.float32, torch.float64)):
+        raise VTError(VT_ERR_INVALID, "vt_autotune_batched: pos must be a CUDA [N,3] float tensor")
+    pos = pos.contiguous()
+    off = np.ascontiguousarray(np.asarray(set_off, dtype=np.int64))
+    bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 6))
+    n_sets = len(off) - 1
+    p = _params(precision, kw.get("k_target", 40), kw.get("max_passes", 1000), kw.get("face_pool", 24), 0)
+    k_out = np.zeros(n_sets, np.int32)
+    t_out = np.zeros(n_sets, np.int32)
+    dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
+    with torch.cuda.device(pos.device):
+        _check(lib.vt_autotune_batched(_ptr(pos), dt, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n_sets,
+                                       bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(p),
+                                       int(sample), _i32p(k_out), _i32p(t_out), _stream_ptr(stream)),
+               "vt_autotune_batched")
+    return k_out, t_out
+
+
 def vt_build_batched(pos, set_off, boxes, mass=None, precision="filter32", k_target=40, max_passes=1000,
-                     face_pool=24, stream=None, radius_policy=0, threads_per_cell=0) -> Handle:
+                     face_pool=24, stream=None, radius_policy=0, threads_per_cell=0, set_k=None,
+                     set_tpc=None) -> Handle:
     """Voronoi cells of independent bounded sets: ``pos`` a CUDA [N,3] tensor, set s the rows
     [set_off[s], set_off[s+1]) inside ``boxes[s] = (lo x, lo y, lo z, hi x, hi y, hi z)``."""
     import numpy as np
@@ -235,13 +270,17 @@ def vt_build_batched(pos, set_off, boxes, mass=None, precision="filter32", k_tar
     if n_sets < 1 or bx.shape[0] != n_sets or off[-1] != pos.shape[0]:
         raise VTError(VT_ERR_INVALID, "vt_build_batched: set_off / boxes / pos sizes disagree")
     p = _params(precision, k_target, max_passes, face_pool, radius_policy, threads_per_cell)
+    sk = None if set_k is None else np.ascontiguousarray(np.asarray(set_k, dtype=np.int32))
+    st = None if set_tpc is None else np.ascontiguousarray(np.asarray(set_tpc, dtype=np.int32))
+    if (sk is not None and sk.shape != (n_sets,)) or (st is not None and st.shape != (n_sets,)):
+        raise VTError(VT_ERR_INVALID, "vt_build_batched: set_k / set_tpc need one entry per set")
     h = ctypes.c_void_p()
     dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
     with torch.cuda.device(pos.device):
         rc = lib.vt_build_batched(ctypes.byref(h), _ptr(pos), dt, _ptr(mass),
                                   off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n_sets,
-                                  bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(p),
-                                  _stream_ptr(stream))
+                                  bx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _i32p(sk), _i32p(st),
+                                  ctypes.byref(p), _stream_ptr(stream))
     if rc != VT_OK:
         part = ctypes.c_int(-1)
         det = lib.vt_last_error_detail(ctypes.byref(part))

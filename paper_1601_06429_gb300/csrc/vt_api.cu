@@ -41,7 +41,8 @@ void free_handle(vt_handle h) {
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     void* ptrs[] = {h->spos, h->perm, h->inv, h->tree_mem, h->cell, h->face_start, h->face_count, h->cstat,
                     h->exact_list, h->dens_sorted, h->faces, h->xws, h->tmp, h->nbr_off_cache, h->dstat,
-                    h->keys, h->keys_alt, h->vals_alt, h->cnt_in, h->sset, h->sgeo, h->soff, h->set_in, h->warp_list};
+                    h->keys, h->keys_alt, h->vals_alt, h->cnt_in, h->sset, h->sgeo, h->soff, h->set_in, h->warp_list,
+                    h->set_cfg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -75,7 +76,9 @@ ClipArgs clip_args(vt_handle h) {
     a.sset = h->sset;
     a.sgeo = h->sgeo;
     a.soff = h->soff;
-    a.warp_list = h->prm.threads_per_cell == 1 ? h->warp_list : nullptr;
+    const bool thread_first = h->set_cfg ? h->any_thread != 0 : h->prm.threads_per_cell == 1;
+    a.warp_list = thread_first ? h->warp_list : nullptr;
+    a.set_cfg = h->set_cfg;
     return a;
 }
 
@@ -203,7 +206,8 @@ void enqueue_sort_tree(vt_handle h, const void* pos, const void* mass) {
 // Shared by vt_build (n_sets == 0: one set, geometry `geo`) and vt_build_batched (n_sets >= 1: the host
 // tables set_off [n_sets+1] and sgeo [n_sets]).
 int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int64_t N, const Geometry& geo,
-               int n_sets, const int64_t* set_off, const Geometry* sgeo_host, const vt_params& prm, void* stream) {
+               int n_sets, const int64_t* set_off, const Geometry* sgeo_host, const int32_t* cfg_host,
+               const vt_params& prm, void* stream) {
     vt_handle h = new (std::nothrow) vt_handle_s;
     if (!h) return VT_ERR_OOM;
     memset(h, 0, sizeof(*h));
@@ -253,6 +257,11 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
         h->set_in = A.get<uint32_t>(N);
         h->sgeo = A.get<Geometry>(n_sets);
         h->soff = A.get<int64_t>(n_sets + 1);
+        if (cfg_host) {
+            h->set_cfg = A.get<int32_t>(n_sets);
+            for (int k = 0; k < n_sets; k++)
+                if ((cfg_host[k] >> 16) & 1) h->any_thread = 1;
+        }
     }
     for (int k = 0; k < 4; k++)
         if (cudaEventCreate(&h->ev[k]) != cudaSuccess) {
@@ -271,6 +280,8 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
         rc = cuda_rc(cudaMemcpyAsync(h->sgeo, sgeo_host, n_sets * sizeof(Geometry), cudaMemcpyHostToDevice, s));
         if (!rc)
             rc = cuda_rc(cudaMemcpyAsync(h->soff, set_off, (n_sets + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        if (!rc && cfg_host)
+            rc = cuda_rc(cudaMemcpyAsync(h->set_cfg, cfg_host, n_sets * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     }
     if (!rc) {
         cudaEventRecord(h->ev[0], s);
@@ -321,11 +332,12 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     Geometry geo;
     rc = make_geometry(box_lo, box_hi, periodic, prm.precision, geo);
     if (rc) return rc;
-    return build_impl(out, pos, dtype, mass, N, geo, 0, nullptr, nullptr, prm, stream);
+    return build_impl(out, pos, dtype, mass, N, geo, 0, nullptr, nullptr, nullptr, prm, stream);
 }
 
 int vt_build_batched(vt_handle* out, const void* pos, int dtype, const void* mass, const int64_t* set_off, int n_sets,
-                     const double* boxes, const vt_params* p, void* stream) {
+                     const double* boxes, const int32_t* set_k, const int32_t* set_tpc, const vt_params* p,
+                     void* stream) {
     if (!out) return VT_ERR_INVALID;
     *out = nullptr;
     if (!pos || !set_off || !boxes || n_sets < 1 || n_sets > VT_MAX_SETS) return VT_ERR_INVALID;
@@ -339,9 +351,126 @@ int vt_build_batched(vt_handle* out, const void* pos, int dtype, const void* mas
     int rc = check_params(p, prm);
     if (rc) return rc;
     Geometry* sg = new (std::nothrow) Geometry[n_sets];
-    if (!sg) return VT_ERR_OOM;
+    int32_t* cfg = (set_k || set_tpc) ? new (std::nothrow) int32_t[n_sets] : nullptr;
+    if (!sg || ((set_k || set_tpc) && !cfg)) {
+        delete[] sg;
+        delete[] cfg;
+        return VT_ERR_OOM;
+    }
     for (int k = 0; k < n_sets && !rc; k++) rc = make_geometry(boxes + 6 * k, boxes + 6 * k + 3, 0, prm.precision, sg[k]);
-    if (!rc) rc = build_impl(out, pos, dtype, mass, N, sg[0], n_sets, set_off, sg, prm, stream);
+    for (int k = 0; cfg && k < n_sets && !rc; k++) {
+        const int kt = set_k ? set_k[k] : prm.k_target;
+        const int tpc = set_tpc ? (set_tpc[k] ? set_tpc[k] : 32) : prm.threads_per_cell;
+        if (kt < 8 || kt > 120 || (tpc != 1 && tpc != 32)) rc = VT_ERR_INVALID;
+        // the thread-per-cell kernel exists for the FP32 filter only
+        cfg[k] = kt | ((tpc == 1 && prm.precision == VT_FILTER32) ? (1 << 16) : 0);
+    }
+    if (!rc) rc = build_impl(out, pos, dtype, mass, N, sg[0], n_sets, set_off, sg, cfg, prm, stream);
+    delete[] sg;
+    delete[] cfg;
+    return rc;
+}
+
+int vt_autotune_batched(const void* pos, int dtype, const int64_t* set_off, int n_sets, const double* boxes,
+                        const vt_params* p, int64_t sample, int32_t* k_out, int32_t* tpc_out, void* stream) {
+    if (!pos || !set_off || !boxes || !k_out || !tpc_out || n_sets < 1 || n_sets > VT_MAX_SETS) return VT_ERR_INVALID;
+    if (dtype != VT_F32 && dtype != VT_F64) return VT_ERR_INVALID;
+    if (set_off[0] != 0) return VT_ERR_INVALID;
+    for (int k = 0; k < n_sets; k++)
+        if (set_off[k + 1] < set_off[k]) return VT_ERR_INVALID;
+    if (set_off[n_sets] < 1 || set_off[n_sets] > 0x7FFFFFFF / 2) return VT_ERR_INVALID;
+    vt_params prm;
+    int rc = check_params(p, prm);
+    if (rc) return rc;
+    if (sample <= 0) sample = 262144;
+    if (sample < 1024) sample = 1024;
+    static const int ks[5] = {16, 24, 32, 48, 64};
+    const int tpcs[2] = {32, 1};
+    const int n_tpc = prm.precision == VT_FILTER32 ? 2 : 1;
+    const size_t row = (dtype == VT_F32 ? sizeof(float) : sizeof(double)) * 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < n_sets; k++) {
+        k_out[k] = prm.k_target;
+        tpc_out[k] = 32;
+    }
+    int* pick = new (std::nothrow) int[n_sets];
+    int64_t* soff = new (std::nothrow) int64_t[n_sets + 1];
+    double* sbox = new (std::nothrow) double[6 * (size_t)n_sets];
+    Geometry* sg = new (std::nothrow) Geometry[n_sets];
+    if (!pick || !soff || !sbox || !sg) rc = VT_ERR_OOM;
+    // size classes [2^c, 2^(c+1))
+    for (int c = 0; c < 31 && !rc; c++) {
+        int64_t npts = 0;
+        int nin = 0;
+        for (int k = 0; k < n_sets; k++) {
+            const int64_t n = set_off[k + 1] - set_off[k];
+            if (n >= ((int64_t)1 << c) && n < ((int64_t)2 << c)) { npts += n; nin++; }
+        }
+        if (nin == 0) continue;
+        // sample: whole sets spread evenly through the class, about `sample` points
+        const int64_t stride = npts > sample ? (npts + sample - 1) / sample : 1;
+        int np = 0, seen = 0;
+        int64_t tot = 0;
+        soff[0] = 0;
+        for (int k = 0; k < n_sets; k++) {
+            const int64_t n = set_off[k + 1] - set_off[k];
+            if (!(n >= ((int64_t)1 << c) && n < ((int64_t)2 << c))) continue;
+            if (seen++ % stride) continue;
+            pick[np] = k;
+            tot += n;
+            soff[np + 1] = tot;
+            for (int q = 0; q < 6; q++) sbox[6 * np + q] = boxes[6 * k + q];
+            np++;
+        }
+        void* buf = nullptr;
+        if (cudaMalloc(&buf, (size_t)tot * row) != cudaSuccess) {
+            cudaGetLastError();
+            rc = VT_ERR_OOM;
+            break;
+        }
+        for (int q = 0; q < np && !rc; q++) {
+            const int k = pick[q];
+            rc = cuda_rc(cudaMemcpyAsync((char*)buf + soff[q] * row, (const char*)pos + set_off[k] * row,
+                                         (size_t)(set_off[k + 1] - set_off[k]) * row, cudaMemcpyDeviceToDevice, s));
+        }
+        for (int q = 0; q < np && !rc; q++) rc = make_geometry(sbox + 6 * q, sbox + 6 * q + 3, 0, prm.precision, sg[q]);
+        // one untimed build, then every configuration; the clipping time decides
+        double best = 1e300;
+        int bk = prm.k_target, bt = 32, last_err = VT_OK;
+        for (int trial = -1; trial < 5 * n_tpc && !rc; trial++) {
+            vt_params t = prm;
+            if (trial >= 0) {
+                t.k_target = ks[trial % 5];
+                t.threads_per_cell = tpcs[trial / 5];
+            }
+            vt_handle h = nullptr;
+            const int e = build_impl(&h, buf, dtype, nullptr, tot, sg[0], np, soff, sg, nullptr, t, stream);
+            if (e) {
+                last_err = e;
+                continue;
+            }
+            const double ms = h->t_clip_ms;
+            cudaStreamSynchronize(h->stream);
+            free_handle(h);
+            if (trial >= 0 && ms < best) {
+                best = ms;
+                bk = t.k_target;
+                bt = t.threads_per_cell;
+            }
+        }
+        cudaFree(buf);
+        if (!rc && best == 1e300) rc = last_err ? last_err : VT_ERR_CUDA;
+        for (int k = 0; k < n_sets && !rc; k++) {
+            const int64_t n = set_off[k + 1] - set_off[k];
+            if (n >= ((int64_t)1 << c) && n < ((int64_t)2 << c)) {
+                k_out[k] = bk;
+                tpc_out[k] = bt;
+            }
+        }
+    }
+    delete[] pick;
+    delete[] soff;
+    delete[] sbox;
     delete[] sg;
     return rc;
 }

@@ -1016,11 +1016,13 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
     // geometry and sorted index range of the cell's point set
     Geometry g = A.geo;
     int64_t slo = 0, shi = A.N;
+    int k_target = A.k_target;
     if (A.sset) {
         const uint32_t s = A.sset[self];
         g = A.sgeo[s];
         slo = A.soff[s];
         shi = A.soff[s + 1];
+        if (A.set_cfg) k_target = A.set_cfg[s] & 0xffff;
     }
     const unsigned lane = lane_id(), lt = lanemask_lt();
     const CT u = Prec<CT>::u();
@@ -1051,7 +1053,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
                 float mn = fminf(d2f, o), mx = fmaxf(d2f, o);
                 d2f = (lower == up) ? mn : mx;
             }
-        int kk = min(max(A.k_target / 4, 4), 30);
+        int kk = min(max(k_target / 4, 4), 30);
         float dk = __shfl_sync(0xffffffffu, d2f, kk);
         if (!(dk < INFINITY)) {
             float mx = d2f < INFINITY ? d2f : 0.f;

@@ -53,7 +53,7 @@ struct TSmem {
 
 // local failure codes (the cell goes to the warp kernel)
 constexpr int TF_CAP = 1, TF_ILL = 2, TF_UNDECIDED = 3, TF_DUP = 4, TF_WALL = 5, TF_RADIUS = 6, TF_CAP_CUT = 7,
-              TF_CAP_PLANES = 8;
+              TF_CAP_PLANES = 8, TF_SKIP = 9;  // TF_SKIP: the cell's set is configured for the warp kernel
 
 __device__ __forceinline__ void tri_ids(uint32_t t, uint32_t& a, uint32_t& b, uint32_t& c) {
     a = t & 255u; b = (t >> 8) & 255u; c = (t >> 16) & 255u;
@@ -590,11 +590,22 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
         const uint32_t self = alive ? (uint32_t)self64 : 0u;
         Geometry g = A.geo;
         int64_t slo = 0, shi = A.N;
+        bool mine = alive;  // the cell's set is configured for this kernel
         if (A.sset && alive) {
             const uint32_t s = A.sset[self];
             g = A.sgeo[s];
             slo = A.soff[s];
             shi = A.soff[s + 1];
+            if (A.set_cfg) mine = ((A.set_cfg[s] >> 16) & 1) != 0;
+        }
+        if (!__any_sync(0xffffffffu, mine)) {
+            // a bucket of warp-kernel sets: hand its cells over as they are
+            const unsigned hm = __ballot_sync(0xffffffffu, alive);
+            unsigned slot0 = 0;
+            if (lane == 0) slot0 = atomicAdd(&A.st->n_warp_cells, (unsigned)__popc(hm));
+            slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+            if (alive) A.warp_list[slot0 + __popc(hm & lt)] = self;
+            continue;
         }
         const P pi = spos[self];
         const float qx = (float)pi.x, qy = (float)pi.y, qz = (float)pi.z;
@@ -659,11 +670,11 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
         float slack = 16.f * u * fmaxf(fmaxf(fmaxf(fabsf(g.hif[0]), fabsf(g.lof[0])), fmaxf(fabsf(g.hif[1]), fabsf(g.lof[1]))),
                                         fmaxf(fmaxf(fabsf(g.hif[2]), fabsf(g.lof[2])), fmaxf(g.Lf[0], fmaxf(g.Lf[1], g.Lf[2])))) + 1e-30f;
         slack = warp_max<float>(alive ? slack : 0.f);
-        int fail = 0;
+        int fail = alive && !mine ? TF_SKIP : 0;
         // start box on the scale of the lane's own neighbourhood (a box that proves too small sends the cell to
         // the warp kernel)
         const float Bown = fminf(4.f * rho, 3.f * sqrtf(near2));
-        if (alive) fail = init_cell<P>(C, g, pi, self, Bown);
+        if (alive && mine) fail = init_cell<P>(C, g, pi, self, Bown);
         bool done = !alive;
         float g2prev = -1.f;
         int streamed = 0;
@@ -791,7 +802,7 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
         const bool emit = alive && !fail;
         // hand the unfinished cells to the warp kernel
         const bool hand = alive && !emit;
-        if (hand) atomicAdd(&A.st->n_tfail[fail > 0 && fail < 8 ? fail : 0], 1ull);  // 0: plane capacity
+        if (hand && fail != TF_SKIP) atomicAdd(&A.st->n_tfail[fail > 0 && fail < 8 ? fail : 0], 1ull);  // 0: plane capacity
         const unsigned hm = __ballot_sync(0xffffffffu, hand);
         if (hm) {
             unsigned slot0 = 0;

@@ -93,6 +93,8 @@ struct vt_handle_s {
     uint32_t* set_in;   // [N] set of each input particle
     vt::Geometry* sgeo; // [n_sets]
     int64_t* soff;      // [n_sets+1] index range of each set (input and sorted order alike)
+    int32_t* set_cfg;   // [n_sets] per-set k_target | thread-per-cell flag << 16, or NULL
+    int any_thread;     // some set takes the thread-per-cell kernel
     // sorted particles
     void* spos;         // float4 (f32) or double4-like 4 doubles (f64): x,y,z,m
     uint32_t* perm;     // sorted -> input index

@@ -56,6 +56,9 @@ struct ClipArgs {
     // FP32 filter: the thread-per-cell kernel runs first and lists here (N entries) the cells the warp kernel
     // must take; NULL: the warp kernel takes every cell
     uint32_t* warp_list;
+    // batched sets: per-set clipping configuration (k_target in the low 16 bits, bit 16: thread-per-cell
+    // kernel first), or NULL for the handle's parameters
+    const int32_t* set_cfg;
 };
 int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s);
 int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);

@@ -134,6 +134,40 @@ def test_batched_varied_boxes_and_degenerate_sets(oracle_mod):
         assert sizes[7] == 2 and np.allclose(vol[two:two + 2], 0.5, rtol=tol)
 
 
+def test_per_set_configuration_matches_oracle(sets64, oracle_mod):
+    """Each set with its own k_target and kernel (thread- or warp-per-cell), mixed in one batch."""
+    pts, off = sets64
+    n_sets = len(off) - 1
+    g = np.random.default_rng(21)
+    set_k = g.choice([16, 24, 32, 48, 64], n_sets).astype(np.int32)
+    set_tpc = g.choice([1, 32], n_sets).astype(np.int32)
+    boxes = unit_boxes(n_sets)
+    pos = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+    h = vt.vt_build_batched(pos, off, boxes, set_k=set_k, set_tpc=set_tpc)
+    vol, noff, ids = vt.cells(h)
+    vol, noff, ids = vol.double().cpu().numpy(), noff.cpu().numpy(), ids.cpu().numpy()
+    for s in range(n_sets):
+        check_set(s, off, boxes[s], vol, noff, ids, pts, oracle_mod, 2e-5)
+
+
+def test_autotune_choices_are_valid_and_change_no_cell(sets64):
+    pts, off = sets64
+    n_sets = len(off) - 1
+    boxes = unit_boxes(n_sets)
+    pos = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
+    set_k, set_tpc = vt.vt_autotune_batched(pos, off, boxes, sample=16384)
+    assert set(set_k.tolist()) <= {16, 24, 32, 48, 64} and set(set_tpc.tolist()) <= {1, 32}
+    # sets of one size class share their choice
+    cls = np.floor(np.log2(np.diff(off))).astype(int)
+    for c in np.unique(cls):
+        assert len(set(zip(set_k[cls == c].tolist(), set_tpc[cls == c].tolist()))) == 1
+    _, v0, o0, i0 = run_batched(pts, off, boxes)
+    h = vt.vt_build_batched(pos, off, boxes, set_k=set_k, set_tpc=set_tpc)
+    v1, o1, i1 = vt.cells(h)
+    assert np.array_equal(o1.cpu().numpy(), o0) and np.array_equal(i1.cpu().numpy(), i0)
+    assert (np.abs(v1.double().cpu().numpy() - v0) <= 4e-5 * v0).all()
+
+
 def test_batched_errors():
     pts, off = inputs.halo_sets(n_sets=4, nmin=64, nmax=256, seed=6, dtype=np.float32)
     boxes = unit_boxes(4)
@@ -151,6 +185,9 @@ def test_batched_errors():
     rev[1], rev[2] = rev[2], rev[1]
     with pytest.raises(vt.VTError) as e:
         vt.vt_build_batched(pos, rev, boxes)
+    assert e.value.code == vt.VT_ERR_INVALID
+    with pytest.raises(vt.VTError) as e:  # k_target out of range for one set
+        vt.vt_build_batched(pos, off, boxes, set_k=np.array([40, 40, 4, 40], np.int32))
     assert e.value.code == vt.VT_ERR_INVALID
 
 
