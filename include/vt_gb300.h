@@ -64,13 +64,13 @@ extern "C" {
 
 typedef struct vt_params {
     int precision;  /* VT_PLAIN64 or VT_FILTER32 (default VT_FILTER32) */
-    int k_target;   /* particles aimed for in a cell's first candidate pass (default 40) */
+    int k_target;   /* particles aimed for in a cell's first candidate pass (default 24) */
     int max_passes; /* candidate radius passes per cell before VT_ERR_SECURITY (default 1000) */
     int face_pool;  /* facet records reserved per particle (default 24; grown on demand) */
     int threads_per_cell; /* VT_FILTER32 only: 32 = one warp per cell (default; 0 means 32); 1 = one thread
                              per cell first, 32 cells of a search-tree bucket per warp, the cells it cannot
                              finish then taken by a warp each (same results) */
-    int reserved[3]; /* [0]: candidate pass sizing, 0 = radius doubling up to 2R (default), 1 = also limited
+    int reserved[3]; /* [0]: candidate pass sizing, 0 = radius doubling up to 2R, 1 = also limited (default)
                         by the density seen so far; others must be 0 */
 } vt_params;
 

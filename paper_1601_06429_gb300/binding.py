@@ -180,7 +180,7 @@ class Handle:
 
 
 def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), periodic=True, precision="filter32",
-             k_target=40, max_passes=1000, face_pool=24, stream=None, radius_policy=0, threads_per_cell=0) -> Handle:
+             k_target=24, max_passes=1000, face_pool=24, stream=None, radius_policy=1, threads_per_cell=0) -> Handle:
     """Voronoi cells of all particles; ``pos`` is a CUDA [N,3] float32/float64 tensor."""
     import torch
 
@@ -236,7 +236,7 @@ def vt_autotune_batched(pos, set_off, boxes, precision="filter32", sample=0, str
     off = np.ascontiguousarray(np.asarray(set_off, dtype=np.int64))
     bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 6))
     n_sets = len(off) - 1
-    p = _params(precision, kw.get("k_target", 40), kw.get("max_passes", 1000), kw.get("face_pool", 24), 0)
+    p = _params(precision, kw.get("k_target", 24), kw.get("max_passes", 1000), kw.get("face_pool", 24), 1)
     k_out = np.zeros(n_sets, np.int32)
     t_out = np.zeros(n_sets, np.int32)
     dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
@@ -248,8 +248,8 @@ def vt_autotune_batched(pos, set_off, boxes, precision="filter32", sample=0, str
     return k_out, t_out
 
 
-def vt_build_batched(pos, set_off, boxes, mass=None, precision="filter32", k_target=40, max_passes=1000,
-                     face_pool=24, stream=None, radius_policy=0, threads_per_cell=0, set_k=None,
+def vt_build_batched(pos, set_off, boxes, mass=None, precision="filter32", k_target=24, max_passes=1000,
+                     face_pool=24, stream=None, radius_policy=1, threads_per_cell=0, set_k=None,
                      set_tpc=None) -> Handle:
     """Voronoi cells of independent bounded sets: ``pos`` a CUDA [N,3] tensor, set s the rows
     [set_off[s], set_off[s+1]) inside ``boxes[s] = (lo x, lo y, lo z, hi x, hi y, hi z)``."""

@@ -142,7 +142,8 @@ int vt_default_params(vt_params* p) {
     if (!p) return VT_ERR_INVALID;
     memset(p, 0, sizeof(*p));
     p->precision = VT_FILTER32;
-    p->k_target = 40;
+    p->k_target = 24;
+    p->reserved[0] = 1;
     p->max_passes = 1000;
     p->face_pool = 24;
     return VT_OK;

@@ -146,9 +146,9 @@ extern "C" int vt_volumes_noalloc(const void* pos, int dtype, int64_t N, const d
     a.N = N;
     a.geo = geo;
     a.tree = tree;
-    a.k_target = 40;
+    a.k_target = 24;
     a.max_passes = 1000;
-    a.radius_policy = 0;
+    a.radius_policy = 1;
     a.cell = cell;
     a.face_start = face_start;
     a.face_count = face_count;

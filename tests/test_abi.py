@@ -2,11 +2,14 @@
 exports every entry point that include/vt_gb300.h declares; argument checks
 that return before any device work behave as documented.  No GPU needed."""
 import ctypes
+import os
 
 import pytest
 
 from paper_1601_06429_gb300 import binding
 from paper_1601_06429_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -25,11 +28,42 @@ def test_exports_every_declared_symbol(lib):
 
 def test_default_params_and_error_strings(lib):
     p = binding.vt_default_params()
-    assert p.precision == binding.VT_FILTER32 and p.k_target == 40 and p.max_passes == 1000 and p.face_pool == 24
+    assert p.precision == binding.VT_FILTER32 and p.k_target == 24 and p.max_passes == 1000 and p.face_pool == 24
+    assert p.threads_per_cell == 0 and list(p.reserved) == [1, 0, 0]
     assert lib.vt_default_params(None) == binding.VT_ERR_INVALID
     for code in range(0, -9, -1):
         assert binding.error_string(code) != "unknown error code"
     assert binding.error_string(-99) == "unknown error code"
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of vt_params and vt_stats have the sizes and field offsets the C compiler
+    gives the header's structs."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {"vt_params": [f for f, _ in binding.vt_params._fields_],
+              "vt_stats": [f for f, _ in binding.vt_stats._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vt_gb300.h"', "int main(void) {"]
+    for s, fs in fields.items():
+        lines.append('printf("%%zu\\n", sizeof(%s));' % s)
+        for f in fs:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (s, f))
+    lines.append("return 0; }")
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for s, fs in fields.items():
+        t = getattr(binding, s)
+        want.append(ctypes.sizeof(t))
+        want += [getattr(t, f).offset for f in fs]
+    assert got == want
 
 
 def test_build_rejects_bad_arguments_without_device_work(lib):
