@@ -200,6 +200,23 @@ def max_over_ranks(v, ws, device=None):
     return float(t.item())
 
 
+HBM_GBS = 6688.8  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+
+
+def step_roofline(N, G, faces, fpc, peak_tflops, t_ms):
+    """Time-based roofline of the whole step: per stage max(bytes / HBM bandwidth, flops / ALU peak), summed,
+    against the measured time (the forward, grid and backward events).  Bytes per cell, algorithmic:
+    key 24, radix sort 6 passes x 32, gather 40, clipping (facet records 32 B each, cell record 24, position 16),
+    neighbour CSR 36 per facet + 8, density 40, gradient 40 per facet + 12, backward 36 per facet + 12; the grid
+    writes 4 B per node."""
+    per_cell = 24 + 6 * 32 + 40 + (32 * faces + 24 + 16) + (36 * faces + 8) + 40 + (40 * faces + 12) + (36 * faces + 12)
+    t_hbm = (per_cell * N + 4.0 * G ** 3) / (HBM_GBS * 1e9) * 1e3
+    t_alu = fpc * N / (peak_tflops * 1e12) * 1e3
+    t_roof = t_hbm + t_alu
+    return {"t_roof_ms": t_roof, "t_hbm_ms": t_hbm, "t_clip_alu_ms": t_alu, "t_measured_ms": t_ms,
+            "frac": t_roof / t_ms, "bytes_per_cell": per_cell}
+
+
 def cpu_oracle_rate(x, L, n_sample, seed=11):
     """The FP64 oracle (certified mode) on n_sample cells of the same point set; returns (cells/s, info)."""
     import oracle
@@ -300,9 +317,13 @@ def run_ours(args):
     grid = torch.empty(G, G, G, dtype=torch.float32, device=dev) if G else None
     dpos = torch.empty(N, 3, dtype=torch.float32, device=dev)
     stats = []
+    marks = []  # per timed step: events after the forward (build, cells, density, gradient), grid, backward
 
-    def step(pos_dev):
+    def step(pos_dev, mark=False):
         nonlocal ids
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if mark else None
+        if ev:
+            ev[0].record(stream)
         if set_off is None:
             h = vt.vt_build(pos_dev, None, box[0], box[1], True, args.precision)
         else:
@@ -313,9 +334,16 @@ def run_ours(args):
         vt.vt_cells(h, vol, off, ids)
         vt.vt_density(h, dens)
         vt.vt_gradient(h, grad)
+        if ev:
+            ev[1].record(stream)
         if G:
             vt.vt_grid_density(h, G, 1, grid)
+        if ev:
+            ev[2].record(stream)
         vt.vt_backward(h, w, 0.0, dpos)
+        if ev:
+            ev[3].record(stream)
+            marks.append(ev)
         st = vt.vt_status(h)
         vt.vt_destroy(h)
         if st["rc"] != 0:
@@ -323,6 +351,8 @@ def run_ours(args):
         stats.append(st)
         return nnz
 
+    # measured FP32 FMA throughput (reported beside the derived peak)
+    probe_tflops = vt.vt_probe_fp32_tflops()
     # ---------------- device-resident inputs
     for _ in range(args.warmup):
         step(xd)
@@ -336,7 +366,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
-        nnz = step(xd)
+        nnz = step(xd, mark=True)
     e1.record(stream)
     torch.cuda.synchronize()
     t_ms = e0.elapsed_time(e1)
@@ -348,6 +378,9 @@ def run_ours(args):
     clip_ms = statistics.mean(s["t_clip_ms"] for s in stats)
     sort_ms = statistics.mean(s["t_sort_ms"] for s in stats)
     launches = sum(s["n_launches"] for s in stats)
+    fwd_ms = statistics.mean(m[0].elapsed_time(m[1]) for m in marks)
+    grid_ms = statistics.mean(m[1].elapsed_time(m[2]) for m in marks)
+    bwd_ms = statistics.mean(m[2].elapsed_time(m[3]) for m in marks)
 
     # ---------------- end to end through the ABI with host buffers
     xh = torch.from_numpy(x).pin_memory()
@@ -404,7 +437,10 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "1 GPU",
                        "l2": "inputs and workspaces larger than L2 (no flush)"},
             "fwd_bwd_breakdown_ms": {"build_sort_tree": sort_ms, "build_clip": clip_ms,
-                                     "rest_of_step": ms_step - sort_ms - clip_ms},
+                                     "rest_of_step": ms_step - sort_ms - clip_ms,
+                                     "forward": fwd_ms, "grid": grid_ms, "backward": bwd_ms},
+            "fwd_cells_per_s": N / (fwd_ms / 1000.0), "bwd_cells_per_s": N / (bwd_ms / 1000.0),
+            "step_roofline": step_roofline(N, G, nnz / N, fpc, peak, fwd_ms + grid_ms + bwd_ms),
             "faces_per_cell": nnz / N,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
@@ -412,7 +448,9 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": CLIP_TRAFFIC.get(args.workload),
                          "kernel": "k_clip (clipping, security test, facet emission)",
                          "work": "%.0f algorithmic flops/cell x %d cells per launch" % (fpc, N),
-                         "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"},
+                         "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                         "peak_probe": probe_tflops,
+                         "frac_of_probe": achieved / probe_tflops if probe_tflops > 0 else None},
             "clocks": clocks,
             "device_counters": {k: stats[-1][k] for k in ("n_cut", "n_tested", "n_passes", "n_fp64_fallbacks",
                                                           "n_exact_cells", "n_exact_preds", "max_faces",

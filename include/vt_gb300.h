@@ -140,6 +140,16 @@ int vt_build(vt_handle *h, const void *pos, int dtype, const void *mass, int64_t
  */
 int vt_rebuild(vt_handle h, const void *pos, const void *mass);
 
+/*
+ * vt_probe_fp32_tflops -- measured FP32 FMA throughput of this GPU (TFLOP/s,
+ * one FMA = 2 flops): eight independent FMA chains per thread on every SM,
+ * best of three timed launches after one untimed (CUDA events).  The
+ * denominator of the clipping kernel's ALU roofline (the paper has no
+ * counterpart).  Synchronises; allocates 16 KB of device memory for the call.
+ * Errors: VT_ERR_INVALID (tflops NULL), VT_ERR_OOM, VT_ERR_CUDA.
+ */
+int vt_probe_fp32_tflops(double *tflops, void *stream);
+
 /* most independent sets one vt_build_batched call takes */
 #define VT_MAX_SETS 65536
 

@@ -109,6 +109,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_volumes_noalloc.argtypes = [P, i32, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        i32, P, P]
     lib.vt_volumes_noalloc.restype = i32
+    lib.vt_probe_fp32_tflops.argtypes = [ctypes.POINTER(ctypes.c_double), P]
+    lib.vt_probe_fp32_tflops.restype = i32
     lib.vt_last_error_detail.argtypes = [ctypes.POINTER(ctypes.c_int)]
     lib.vt_last_error_detail.restype = i32
     lib.vt_error_string.argtypes = [i32]
@@ -147,6 +149,13 @@ def _stream_ptr(stream):
 
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def vt_probe_fp32_tflops(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU in TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(load_library().vt_probe_fp32_tflops(ctypes.byref(v), _stream_ptr(stream)), "vt_probe_fp32_tflops")
+    return float(v.value)
 
 
 def vt_last_error_detail():

@@ -601,6 +601,44 @@ int vt_status(vt_handle h, vt_stats* out) {
     return d.error ? d.error : VT_OK;
 }
 
+int vt_probe_fp32_tflops(double* tflops, void* stream) {
+    if (!tflops) return VT_ERR_INVALID;
+    *tflops = 0.0;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    float* sink = nullptr;
+    if (cudaMalloc((void**)&sink, 4096 * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_OOM;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = sms * 8, iters = 4096;
+    double best = 0.0;
+    int rc = VT_OK;
+    for (int rep = 0; rep < 4 && !rc; rep++) {
+        cudaEventRecord(e0, s);
+        launch_fma_probe(blocks, iters, sink, s);
+        cudaEventRecord(e1, s);
+        rc = cuda_rc(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        if (!rc && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f && rep > 0) {
+            const double flops = 2.0 * 8.0 * 16.0 * iters * (double)blocks * 256.0;
+            const double t = flops / (ms * 1e-3) / 1e12;
+            if (t > best) best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (!rc) rc = cuda_rc(cudaGetLastError());
+    *tflops = best;
+    return rc;
+}
+
 int vt_last_error_detail(int* particle) {
     if (particle) *particle = g_last_particle;
     return g_last_detail;

@@ -63,6 +63,7 @@ struct ClipArgs {
 int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s);
 int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
 int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
+int launch_fma_probe(int blocks, int iters, float* sink, cudaStream_t s);
 size_t exact_ws_doubles_per_warp();
 
 // post-processing (vt_post.cu)

@@ -417,3 +417,28 @@ int launch_backward(const Face* faces, const uint32_t* face_start, const uint16_
 }
 
 }  // namespace vt
+
+namespace vt {
+// ------------------------------------------------------------------ FP32 FMA throughput probe
+// Eight independent FMA chains per thread, long enough that issue, not latency, bounds the loop; the result is
+// written only if it is impossible (never), so the compiler keeps the work.
+__global__ void __launch_bounds__(256) k_fma_probe(float seed, int iters, float* sink) {
+    float a0 = seed + threadIdx.x, a1 = a0 + 1.f, a2 = a0 + 2.f, a3 = a0 + 3.f, a4 = a0 + 4.f, a5 = a0 + 5.f,
+          a6 = a0 + 6.f, a7 = a0 + 7.f;
+    const float m = 0.999999f, c = 1e-7f;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            a0 = __fmaf_rn(a0, m, c); a1 = __fmaf_rn(a1, m, c); a2 = __fmaf_rn(a2, m, c); a3 = __fmaf_rn(a3, m, c);
+            a4 = __fmaf_rn(a4, m, c); a5 = __fmaf_rn(a5, m, c); a6 = __fmaf_rn(a6, m, c); a7 = __fmaf_rn(a7, m, c);
+        }
+    }
+    const float r = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    if (r == -1.2345f) sink[blockIdx.x] = r;
+}
+
+int launch_fma_probe(int blocks, int iters, float* sink, cudaStream_t s) {
+    k_fma_probe<<<blocks, 256, 0, s>>>(1.f, iters, sink);
+    return 1;
+}
+}  // namespace vt
