@@ -845,6 +845,11 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
     float slack = 2.0f * 1.2e-7f * fmaxf(fmaxf(fabsf(g.hif[0]), fabsf(g.lof[0])),
                                          fmaxf(fmaxf(fabsf(g.hif[1]), fabsf(g.lof[1])),
                                                fmaxf(fabsf(g.hif[2]), fabsf(g.lof[2]))));
+    // a search ball that stays inside the periodic box meets no image across it: the node tests then need no
+    // shifted copies (points beyond the box are farther than the radius in their minimum image too)
+    const float reach = rad + 4.f * slack;
+    const int per = g.periodic && !(qx - reach > g.lof[0] && qx + reach < g.hif[0] && qy - reach > g.lof[1] &&
+                                    qy + reach < g.hif[1] && qz - reach > g.lof[2] && qz + reach < g.hif[2]);
     int sp = 0;
     int top = t.levels;
     {
@@ -853,14 +858,14 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
         const int64_t span_top = (int64_t)1 << (5 * top);
         if ((int64_t)lane < nt && lane * span_top < shi && (lane + 1) * span_top > slo) {
             float4 lo = t.lo[t.off[top] + lane], hi = t.hi[t.off[top] + lane];
-            float dx = fmaxf(axis_gap(qx, lo.x, hi.x, g.Lf[0], g.periodic) - slack, 0.f);
-            float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], g.periodic) - slack, 0.f);
-            float dz = fmaxf(axis_gap(qz, lo.z, hi.z, g.Lf[2], g.periodic) - slack, 0.f);
+            float dx = fmaxf(axis_gap(qx, lo.x, hi.x, g.Lf[0], per) - slack, 0.f);
+            float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], per) - slack, 0.f);
+            float dz = fmaxf(axis_gap(qz, lo.z, hi.z, g.Lf[2], per) - slack, 0.f);
             hit = dx * dx + dy * dy + dz * dz <= rad2;
             if (hit) {
-                float sx = supp_axis(qx, lo.x - slack, hi.x + slack, g.Lf[0], g.periodic, bmin[0], bmax[0]);
-                float sy = supp_axis(qy, lo.y - slack, hi.y + slack, g.Lf[1], g.periodic, bmin[1], bmax[1]);
-                float sz = supp_axis(qz, lo.z - slack, hi.z + slack, g.Lf[2], g.periodic, bmin[2], bmax[2]);
+                float sx = supp_axis(qx, lo.x - slack, hi.x + slack, g.Lf[0], per, bmin[0], bmax[0]);
+                float sy = supp_axis(qy, lo.y - slack, hi.y + slack, g.Lf[1], per, bmin[1], bmax[1]);
+                float sz = supp_axis(qz, lo.z - slack, hi.z + slack, g.Lf[2], per, bmin[2], bmax[2]);
                 if (sx + sy + sz < -stol) hit = false;
             }
         }
@@ -919,22 +924,22 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
             const int64_t span = (int64_t)1 << (5 * cl);  // sorted particles under a node of level cl
             if (c < t.count[cl] && c * span < shi && (c + 1) * span > slo) {
                 float4 lo = t.lo[t.off[cl] + c], hi = t.hi[t.off[cl] + c];
-                float dx = fmaxf(axis_gap(qx, lo.x, hi.x, g.Lf[0], g.periodic) - slack, 0.f);
-                float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], g.periodic) - slack, 0.f);
-                float dz = fmaxf(axis_gap(qz, lo.z, hi.z, g.Lf[2], g.periodic) - slack, 0.f);
+                float dx = fmaxf(axis_gap(qx, lo.x, hi.x, g.Lf[0], per) - slack, 0.f);
+                float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], per) - slack, 0.f);
+                float dz = fmaxf(axis_gap(qz, lo.z, hi.z, g.Lf[2], per) - slack, 0.f);
                 hit = dx * dx + dy * dy + dz * dz <= rad2;
                 if (hit && inner2 > 0.f) {
                     // every point of the node already examined in an earlier pass: skip it
-                    float fx = axis_far(qx, lo.x, hi.x, g.Lf[0], g.periodic) + slack;
-                    float fy = axis_far(qy, lo.y, hi.y, g.Lf[1], g.periodic) + slack;
-                    float fz = axis_far(qz, lo.z, hi.z, g.Lf[2], g.periodic) + slack;
+                    float fx = axis_far(qx, lo.x, hi.x, g.Lf[0], per) + slack;
+                    float fy = axis_far(qy, lo.y, hi.y, g.Lf[1], per) + slack;
+                    float fz = axis_far(qz, lo.z, hi.z, g.Lf[2], per) + slack;
                     if (fx * fx + fy * fy + fz * fz < inner2) hit = false;
                 }
                 if (hit) {
                     // no point of the node can cut the cell (node widened by the rounding slack of q)
-                    float sx = supp_axis(qx, lo.x - slack, hi.x + slack, g.Lf[0], g.periodic, bmin[0], bmax[0]);
-                    float sy = supp_axis(qy, lo.y - slack, hi.y + slack, g.Lf[1], g.periodic, bmin[1], bmax[1]);
-                    float sz = supp_axis(qz, lo.z - slack, hi.z + slack, g.Lf[2], g.periodic, bmin[2], bmax[2]);
+                    float sx = supp_axis(qx, lo.x - slack, hi.x + slack, g.Lf[0], per, bmin[0], bmax[0]);
+                    float sy = supp_axis(qy, lo.y - slack, hi.y + slack, g.Lf[1], per, bmin[1], bmax[1]);
+                    float sz = supp_axis(qz, lo.z - slack, hi.z + slack, g.Lf[2], per, bmin[2], bmax[2]);
                     if (sx + sy + sz < -stol) hit = false;
                 }
             }
