@@ -48,8 +48,9 @@ struct Cap {
     static constexpr int MAXP = TP <= 4 ? 128 : 512;
     static constexpr uint32_t IDM = (1u << IDB) - 1u;
     static constexpr int SB = TP <= 4 ? 7 : 9;            // bits of a vertex slot
-    static constexpr int CAND = TP <= 4 ? 128 : 256;      // candidates per radius pass
+    static constexpr int CAND = TP <= 4 ? 128 : 256;      // candidates per radius pass (a power of two: sort_cand)
     static constexpr int STACK = TP <= 4 ? STACK_CAP : 4 * STACK_CAP;
+    static_assert((CAND & (CAND - 1)) == 0, "sort_cand pads the candidates to a power of two up to CAND");
 };
 constexpr int CHUNK = 4;
 constexpr int EXACT_WS = 12288;  // doubles per warp for expansion arithmetic
@@ -983,6 +984,15 @@ constexpr int RC_NEED_EXACT = 1000;
 constexpr int RC_POOL = 1001;
 constexpr int RC_RETRY_BOX = 1002;
 
+// any of the six start planes an artificial wall (the small start box)
+template <typename CT, int TP>
+__device__ __forceinline__ bool art_walls(const WarpSmem<CT, TP>& S) {
+    bool a = false;
+#pragma unroll
+    for (int k = 0; k < 6; k++) a |= S.pcode[k] >= CODE_ART;
+    return a;
+}
+
 // successor of triangle t around plane p: the neighbour across the edge (corner before p) -> p
 template <typename CT, int TP>
 __device__ __forceinline__ uint32_t succ_tri(const WarpSmem<CT, TP>& S, uint32_t t, int p) {
@@ -1283,7 +1293,9 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         if (rhi2 * ((CT)1 - (CT)8 * u) >= (CT)4 * R2) { done = true; break; }
         // an ill-conditioned vertex (infinite error bound) blocks the certificate: redo the cell in FP64
         if (!EXACT && !(R2 < (CT)INFINITY)) return RC_NEED_EXACT;
-        if (rhi2 >= cap2) return g.periodic ? VT_ERR_UNSUPPORTED : VT_ERR_SECURITY;
+        // the widest search did not certify the cell: if an artificial wall of the small start box still bounds
+        // it (a cell in a void larger than the box), redo it from the true walls; otherwise give up
+        if (rhi2 >= cap2) return art_walls(S) ? RC_RETRY_BOX : g.periodic ? VT_ERR_UNSUPPORTED : VT_ERR_SECURITY;
         // next pass: the annulus up to 2R, at most twice the radius (policy 1: also no further than the radius
         // that the density seen so far says holds about 3/4 of a pass's capacity)
         {
@@ -1301,7 +1313,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             rhi2 = nxt < (CT)lim ? nxt : (CT)lim;
         }
     }
-    if (!done) return (!EXACT && !(R2 < (CT)INFINITY)) ? RC_NEED_EXACT : VT_ERR_SECURITY;
+    if (!done) return art_walls(S) ? RC_RETRY_BOX : (!EXACT && !(R2 < (CT)INFINITY)) ? RC_NEED_EXACT : VT_ERR_SECURITY;
     if (g.periodic && !((CT)16 * R2 < (CT)(lmin * lmin))) return VT_ERR_UNSUPPORTED;
 
     // ---------------- emission: one triangle per plane present, then walks along the adjacency
