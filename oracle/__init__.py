@@ -199,6 +199,34 @@ def gradient(dens_self, nbr_off, nbr_ids, disp, dens_all):
     return g
 
 
+def gradient_green_gauss(res, pos, dens_self, dens_all, box_lo=0.0, box_hi=1.0):
+    """Green-Gauss density gradient (the Voronoi form of moving-mesh codes, cited in the Introduction):
+    the divergence theorem over the cell, grad rho_i = (1/V_i) * surface integral of rho n, with rho at each
+    facet centroid interpolated linearly between the two sites and rho_i on box walls.  Using
+    sum_f A_f n_f = 0 and sum_f A_f (c_f - m_f) x n_f = 0 on a closed cell this becomes
+    ``(1/V_i) sum_f A_f (rho_j - rho_i) c_f / |d_f|`` over the facets between particles, c_f the facet
+    centroid relative to x_i, d_f the image displacement; facets with the cell's own images add nothing.
+    ``dens_self[k]`` is rho_i of the k-th listed cell, ``dens_all`` indexes rho_j by particle id."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    lo, hi = _box(box_lo, box_hi)
+    L = hi - lo
+    dens_all = np.asarray(dens_all, dtype=np.float64)
+    off = res["face_off"]
+    n = len(off) - 1
+    owner = np.repeat(np.arange(n), np.diff(off))
+    i = res["which"][owner]
+    j = res["f_nbr"]
+    inner = j >= 0
+    d = pos[np.where(inner, j, 0)] + res["f_shift"] * L[None, :] - pos[i]
+    r = np.sqrt((d * d).sum(1))
+    c = res["f_cen"] - pos[i]
+    w = np.where(inner, res["f_area"] * (dens_all[np.where(inner, j, 0)] - np.asarray(dens_self)[owner]) /
+                 np.where(inner, r, 1.0), 0.0)
+    g = np.zeros((n, 3))
+    np.add.at(g, owner, w[:, None] * c)
+    return g / res["vol"][:, None]
+
+
 def grid_nearest(pos, box_lo, box_hi, G, S=1, periodic=True, nthreads=0):
     """Index of the nearest particle for every node sub-point of a G^3 grid
     (brute force; ties to the lower index).  Returns [G^3, S^3] int64, node
