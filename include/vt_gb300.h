@@ -229,6 +229,16 @@ int vt_density(vt_handle h, void *dens);
 int vt_gradient(vt_handle h, void *grad);
 
 /*
+ * vt_gradient_gg -- the Green-Gauss form of the density gradient, as used by
+ * the moving-mesh code the Introduction cites among uses of the tessellation:
+ *   grad rho_i = (1/V_i) sum_f A_f (rho_j - rho_i) c_f / |d_f|
+ * over the facets between particles (c_f the facet centroid relative to x_i,
+ * d_f the neighbour image's displacement); exact for a linear density field;
+ * on a wall of a bounded box rho is taken as rho_i.  grad: device [N][3].
+ */
+int vt_gradient_gg(vt_handle h, void *grad);
+
+/*
  * vt_grid_density -- densities on a regular G^3 grid over the box
  * (Implementation section; the paper gives no formula): node (a,b,c) takes
  * the mean, over its S^3 stratified sub-points

@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_density.restype = i32
     lib.vt_gradient.argtypes = [P, P]
     lib.vt_gradient.restype = i32
+    lib.vt_gradient_gg.argtypes = [P, P]
+    lib.vt_gradient_gg.restype = i32
     lib.vt_grid_density.argtypes = [P, i32, i32, P]
     lib.vt_grid_density.restype = i32
     lib.vt_moments.argtypes = [P, P, P]
@@ -328,6 +330,10 @@ def vt_gradient(h: Handle, grad) -> None:
     _check(load_library().vt_gradient(h.ptr, _ptr(grad)), "vt_gradient")
 
 
+def vt_gradient_gg(h: Handle, grad) -> None:
+    _check(load_library().vt_gradient_gg(h.ptr, _ptr(grad)), "vt_gradient_gg")
+
+
 def vt_grid_density(h: Handle, G: int, S: int, grid) -> None:
     _check(load_library().vt_grid_density(h.ptr, int(G), int(S), _ptr(grid)), "vt_grid_density")
 
@@ -395,6 +401,14 @@ def gradient(h: Handle):
 
     g = torch.empty(h.N, 3, dtype=h.dtype, device=h.device)
     vt_gradient(h, g)
+    return g
+
+
+def gradient_gg(h: Handle):
+    import torch
+
+    g = torch.empty(h.N, 3, dtype=h.dtype, device=h.device)
+    vt_gradient_gg(h, g)
     return g
 
 

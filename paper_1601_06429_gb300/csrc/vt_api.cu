@@ -540,6 +540,15 @@ int vt_gradient(vt_handle h, void* grad) {
     return cuda_rc(cudaGetLastError());
 }
 
+int vt_gradient_gg(vt_handle h, void* grad) {
+    if (!h || !grad) return VT_ERR_INVALID;
+    int rc = ensure_density(h);
+    if (rc) return rc;
+    h->n_launches += launch_gradient_gg(h->faces, h->face_start, h->face_count, h->cell, h->dens_sorted, h->perm, h->N,
+                                        grad, h->dtype, h->stream);
+    return cuda_rc(cudaGetLastError());
+}
+
 int vt_grid_density(vt_handle h, int G, int S, void* grid) {
     if (!h || !grid || G < 1 || G > 4096 || S < 1 || S > 8) return VT_ERR_INVALID;
     if ((int64_t)G * G * G > ((int64_t)1 << 34)) return VT_ERR_INVALID;

@@ -64,6 +64,9 @@ int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaS
 int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
 int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
 int launch_fma_probe(int blocks, int iters, float* sink, cudaStream_t s);
+int launch_gradient_gg(const Face* faces, const uint32_t* face_start, const uint16_t* face_count, const CellOut* cell,
+                       const double* dens_sorted, const uint32_t* perm, int64_t N, void* grad, int dtype,
+                       cudaStream_t s);
 size_t exact_ws_doubles_per_warp();
 
 // post-processing (vt_post.cu)

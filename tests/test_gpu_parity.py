@@ -160,6 +160,33 @@ def test_clustered64k_all_cells(clustered64k, oracle_mod, prec, tol, tpc):
     check_gradient(g, x, o, oracle_mod, np.arange(len(x)), 0.0, L, floor, 1e-4)
 
 
+# ---------------------------------------------------------------- Green-Gauss gradient
+@pytest.mark.parametrize("prec,floor", [("plain64", 1e-3), ("filter32", 1e-1)])
+def test_green_gauss_gradient_matches_oracle(uniform4096, oracle_mod, prec, floor):
+    x, o = uniform4096
+    h = vt.vt_build(torch.from_numpy(x).cuda(), None, (0.0,) * 3, (1.0,) * 3, True, prec)
+    got = vt.gradient_gg(h).double().cpu().numpy()
+    dens_o = 1.0 / o["vol"]
+    ref = oracle_mod.gradient_green_gauss(o, x, dens_o, dens_o, 0.0, 1.0)
+    ell = o["vol"] ** (1.0 / 3.0)
+    den = np.maximum(np.linalg.norm(ref, axis=1), floor * dens_o / ell)
+    assert (np.linalg.norm(got - ref, axis=1) / den).max() <= 1e-4
+
+
+def test_green_gauss_gradient_of_a_linear_density(oracle_mod):
+    """Masses chosen so that the density is a linear field (m_i = phi(x_i) V_i with the oracle's volumes): the
+    GPU Green-Gauss gradient recovers the field's gradient on every cell no wall bounds."""
+    x = inputs.uniform(3000, seed=13)
+    o = oracle_mod.cells(x, 0.0, 1.0, False, mode="certified")
+    g_true = np.array([0.3, -1.7, 2.5])
+    m = (4.0 + x @ g_true) * o["vol"]
+    h = vt.vt_build(torch.from_numpy(x).cuda(), torch.from_numpy(m).cuda(), (0.0,) * 3, (1.0,) * 3, False, "plain64")
+    got = vt.gradient_gg(h).double().cpu().numpy()
+    off = o["face_off"]
+    interior = np.array([(o["f_nbr"][off[k]:off[k + 1]] >= 0).all() for k in range(len(x))])
+    assert np.abs(got[interior] - g_true[None, :]).max() < 1e-3
+
+
 # ---------------------------------------------------------------- bounded box
 def test_bounded_halo_sets(oracle_mod):
     pts, off = inputs.halo_sets(n_sets=3, nmin=300, nmax=5000, seed=6, dtype=np.float32)
