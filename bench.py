@@ -52,7 +52,7 @@ WORK = {
 }
 # DRAM bytes (read + write) of one launch of the clipping kernel, from one ncu capture of this kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/launches_clustered16M.md)
-CLIP_TRAFFIC = {"clustered16M": 10.488e9}
+CLIP_TRAFFIC = {("clustered16M", "filter32"): 10.488e9}
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
 
@@ -445,12 +445,15 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": CLIP_TRAFFIC.get(args.workload),
+                         "frac": achieved / peak, "traffic": CLIP_TRAFFIC.get((args.workload, args.precision)),
                          "kernel": "k_clip (clipping, security test, facet emission)",
                          "work": "%.0f algorithmic flops/cell x %d cells per launch" % (fpc, N),
-                         "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
-                         "peak_probe": probe_tflops,
-                         "frac_of_probe": achieved / probe_tflops if probe_tflops > 0 else None},
+                         "peak_note": ("FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"
+                                       if args.precision == "filter32" else
+                                       "FP64: 1/64 of the FP32 FMA issue rate, 80.5 / 64 TFLOP/s (derived)"),
+                         "peak_probe": probe_tflops if args.precision == "filter32" else None,
+                         "frac_of_probe": achieved / probe_tflops if probe_tflops > 0 and args.precision == "filter32"
+                         else None},
             "clocks": clocks,
             "device_counters": {k: stats[-1][k] for k in ("n_cut", "n_tested", "n_passes", "n_fp64_fallbacks",
                                                           "n_exact_cells", "n_exact_preds", "max_faces",

@@ -266,3 +266,7 @@ def test_clustered_16M_sampled(oracle_mod):
     x = inputs.clustered(16777216, L=200.0, seed=2)
     g = _sampled(x, 200.0, "filter32", 2e-5, oracle_mod, 2048, 7)
     assert g["stats"]["device_error"] == 0
+    del g
+    # the same workload on the plain FP64 path
+    g = _sampled(x, 200.0, "plain64", 1e-6, oracle_mod, 1024, 8)
+    assert g["stats"]["device_error"] == 0
