@@ -167,7 +167,9 @@ typedef struct {
 
 /* A plane  n . y <= h  in the frame centred on x_i.
  * kind 0: bisector with point j under image shift s:  n = d, h = |d|^2/2.
- * kind 1: wall (bounded box), wall index w = 2*axis + (0: upper, 1: lower). */
+ * kind 1: wall (bounded box), wall index w = 2*axis + (0: upper, 1: lower).
+ * kind 2: voxel wall at the absolute coordinate bnd + sl along the axis of w
+ *         (bnd a grid coordinate, sl a periodic shift), same orientation as a wall. */
 typedef struct {
     double n[3], h;
     ivl ni[3], hi;
@@ -176,6 +178,7 @@ typedef struct {
     int s[3];
     int w;
     double key_lo; /* rigorous lower bound of |d|^2 (bisectors) */
+    double bnd, sl; /* voxel walls */
 } plane_t;
 
 typedef struct {
@@ -223,12 +226,21 @@ static void exact_row(const cellwork *cw, const plane_t *p, xpn row[4]) {
             for (int k = 0; k < d[c].n; k++) xp_add_d(&row[c], 2.0 * d[c].c[k]);
             xp_addmul(&row[3], &d[c], &d[c], +1);
         }
-    } else {
+    } else if (p->kind == 1) {
         int axis = p->w / 2, upper = (p->w % 2) == 0;
         for (int c = 0; c < 3; c++) xp_set_d(&row[c], c == axis ? (upper ? 1.0 : -1.0) : 0.0);
         xp_zero(&row[3]);
         if (upper) { xp_add_d(&row[3], pb->hi[axis]); xp_add_d(&row[3], -pb->x[3 * cw->i + axis]); }
         else { xp_add_d(&row[3], pb->x[3 * cw->i + axis]); xp_add_d(&row[3], -pb->lo[axis]); }
+    } else {
+        int axis = p->w / 2, upper = (p->w % 2) == 0;
+        double sg = upper ? 1.0 : -1.0;
+        for (int c = 0; c < 3; c++) xp_set_d(&row[c], c == axis ? sg : 0.0);
+        /* h = sg (bnd + sl - x_i), exactly */
+        xp_zero(&row[3]);
+        xp_add_d(&row[3], sg * p->bnd);
+        if (p->sl != 0.0) xp_add_d(&row[3], sg * p->sl);
+        xp_add_d(&row[3], -sg * pb->x[3 * cw->i + axis]);
     }
 }
 
@@ -313,6 +325,22 @@ static void make_wall(const problem *pb, int64_t i, int w, plane_t *p) {
     double xi = pb->x[3 * i + axis];
     if (upper) { p->h = pb->hi[axis] - xi; p->hi = iv_sub(iv_pt(pb->hi[axis]), iv_pt(xi)); }
     else { p->h = xi - pb->lo[axis]; p->hi = iv_sub(iv_pt(xi), iv_pt(pb->lo[axis])); }
+    p->key_lo = 0.0;
+}
+
+/* voxel wall w (2*axis + 0 upper / 1 lower) at absolute coordinate bnd + sl */
+static void make_voxel_wall(const problem *pb, int64_t i, int w, double bnd, double sl, plane_t *p) {
+    int axis = w / 2, upper = (w % 2) == 0;
+    p->kind = 2; p->j = -1; p->w = w; p->s[0] = p->s[1] = p->s[2] = 0;
+    p->bnd = bnd; p->sl = sl;
+    for (int c = 0; c < 3; c++) {
+        double val = (c == axis) ? (upper ? 1.0 : -1.0) : 0.0;
+        p->n[c] = val; p->ni[c] = iv_pt(val);
+    }
+    double xi = pb->x[3 * i + axis];
+    ivl b = iv_add(iv_pt(bnd), iv_pt(sl));
+    if (upper) { p->h = (bnd + sl) - xi; p->hi = iv_sub(b, iv_pt(xi)); }
+    else { p->h = xi - (bnd + sl); p->hi = iv_sub(iv_pt(xi), b); }
     p->key_lo = 0.0;
 }
 
@@ -977,6 +1005,143 @@ void oracle_grid_point(const double *box_lo, const double *box_hi, int G, int S,
     g[0] = box_lo[0] + ((double)a + ((double)u + 0.5) / S) * (L[0] / G);
     g[1] = box_lo[1] + ((double)b + ((double)v + 0.5) / S) * (L[1] / G);
     g[2] = box_lo[2] + ((double)c + ((double)w + 0.5) / S) * (L[2] / G);
+}
+
+/*
+ * oracle_grid_volume: the volume-weighted average of the cell densities over
+ * each voxel of a regular G^3 grid (the exact reading of the Implementation
+ * section's average Voronoi densities on a grid):
+ *     grid[v] = sum_i dens[i] |V_i intersect voxel v| / |voxel v|,
+ * voxel (a, b, c) = [lo + a h, lo + (a+1) h] per axis, h = L / G (FP64), the
+ * coordinates computed as lo + a * h; periodic boxes wrap the voxel indices.
+ * Each cell is computed as in oracle_cells (certified mode) and clipped, for
+ * every voxel that its box meets, by the voxel's six walls with the same
+ * exact predicates; the volume of what remains is the overlap.
+ *   grid  [G][G][G] out, index (c * G + b) * G + a (x fastest)
+ * counters[0..3] as in oracle_cells.  Returns 0 or the first error code.
+ */
+int oracle_grid_volume(int64_t N, const double *pos, const double *box_lo, const double *box_hi, int periodic,
+                       int G, const double *dens, double *grid, int64_t *counters, int nthreads) {
+    problem pb;
+    pb.N = N; pb.x = pos; pb.periodic = periodic;
+    for (int c = 0; c < 3; c++) { pb.lo[c] = box_lo[c]; pb.hi[c] = box_hi[c]; pb.L[c] = box_hi[c] - box_lo[c]; }
+    double h[3];
+    for (int c = 0; c < 3; c++) h[c] = pb.L[c] / G;
+    const int64_t G3 = (int64_t)G * G * G;
+    for (int64_t v = 0; v < G3; v++) grid[v] = 0.0;
+    kdtree tree;
+    kd_build(&tree, &pb);
+    int64_t *leaf_of = (int64_t *)malloc(sizeof(int64_t) * (N > 0 ? N : 1));
+    for (int64_t n = 0; n < tree.nn; n++)
+        if (tree.nd[n].left < 0)
+            for (int64_t k = tree.nd[n].a; k < tree.nd[n].b; k++) leaf_of[tree.idx[k]] = n;
+    int64_t tot_pred = 0, tot_exact = 0, tot_zero = 0, tot_err = 0;
+    int first_err = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel reduction(+ : tot_pred, tot_exact, tot_zero, tot_err)
+    {
+        cellwork cw, cv;
+        cw.pb = &pb; cv.pb = &pb;
+        cw.pl = (plane_t *)malloc(sizeof(plane_t) * MAXP);
+        cw.v = (vert_t *)malloc(sizeof(vert_t) * MAXV);
+        cw.tmp = (vert_t *)malloc(sizeof(vert_t) * MAXV);
+        cw.side = (int8_t *)malloc(MAXV);
+        cv.pl = (plane_t *)malloc(sizeof(plane_t) * MAXP);
+        cv.v = (vert_t *)malloc(sizeof(vert_t) * MAXV);
+        cv.tmp = (vert_t *)malloc(sizeof(vert_t) * MAXV);
+        cv.side = (int8_t *)malloc(MAXV);
+        int64_t *f_nbr = (int64_t *)malloc(sizeof(int64_t) * MAXP);
+        int32_t *f_shift = (int32_t *)malloc(sizeof(int32_t) * 3 * MAXP);
+        double *f_area = (double *)malloc(sizeof(double) * MAXP);
+        double *f_cen = (double *)malloc(sizeof(double) * 3 * MAXP);
+        double *f_dist = (double *)malloc(sizeof(double) * MAXP);
+        candbuf cb = {NULL, 0, 0};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t i = 0; i < N; i++) {
+            cw.i = i;
+            init_cell(&cw);
+            int rc = run_certified(&cw, &tree, &cb, leaf_of[i]);
+            tot_pred += cw.n_pred; tot_exact += cw.n_exact; tot_zero += cw.n_zero;
+            if (rc != 0) {
+                tot_err++;
+#pragma omp critical
+                { if (!first_err) first_err = rc; }
+                continue;
+            }
+            /* voxel index range of the cell's enclosing box */
+            int64_t a0[3], a1[3];
+            for (int c = 0; c < 3; c++) {
+                double mn = INFINITY, mx = -INFINITY;
+                for (int k = 0; k < cw.nv; k++) {
+                    mn = fmin(mn, cw.v[k].yi[c].lo);
+                    mx = fmax(mx, cw.v[k].yi[c].hi);
+                }
+                double xi = pos[3 * i + c];
+                a0[c] = (int64_t)floor((xi + mn - pb.lo[c]) / h[c]) - 1;
+                a1[c] = (int64_t)floor((xi + mx - pb.lo[c]) / h[c]) + 1;
+                if (!periodic) {
+                    if (a0[c] < 0) a0[c] = 0;
+                    if (a1[c] > G - 1) a1[c] = G - 1;
+                }
+            }
+            for (int64_t az = a0[2]; az <= a1[2]; az++)
+                for (int64_t ay = a0[1]; ay <= a1[1]; ay++)
+                    for (int64_t ax = a0[0]; ax <= a1[0]; ax++) {
+                        int64_t ia[3] = {ax, ay, az}, v[3];
+                        double sl[3];
+                        for (int c = 0; c < 3; c++) {
+                            int64_t q = ia[c] % G;
+                            if (q < 0) q += G;
+                            v[c] = q;
+                            sl[c] = (double)((ia[c] - q) / G) * pb.L[c];
+                        }
+                        /* copy of the cell, clipped by the voxel's six walls */
+                        cv.i = i; cv.np = cw.np; cv.nv = cw.nv; cv.err = 0;
+                        cv.n_pred = cv.n_exact = cv.n_zero = cv.n_tested = cv.n_cut = 0;
+                        memcpy(cv.pl, cw.pl, sizeof(plane_t) * cw.np);
+                        memcpy(cv.v, cw.v, sizeof(vert_t) * cw.nv);
+                        for (int w = 0; w < 6 && cv.nv > 0 && !cv.err; w++) {
+                            int axis = w / 2, upper = (w % 2) == 0;
+                            double bnd = pb.lo[axis] + (double)(v[axis] + (upper ? 1 : 0)) * h[axis];
+                            plane_t pw;
+                            make_voxel_wall(&pb, i, w, bnd, sl[axis], &pw);
+                            clip(&cv, &pw);
+                        }
+                        tot_pred += cv.n_pred; tot_exact += cv.n_exact; tot_zero += cv.n_zero;
+                        if (cv.err) {
+                            tot_err++;
+#pragma omp critical
+                            { if (!first_err) first_err = cv.err; }
+                            continue;
+                        }
+                        if (cv.nv == 0) continue;
+                        cellout co;
+                        memset(&co, 0, sizeof(co));
+                        int e = extract(&cv, &co, MAXP, f_nbr, f_shift, f_area, f_cen, f_dist);
+                        if (e) {
+                            tot_err++;
+#pragma omp critical
+                            { if (!first_err) first_err = e; }
+                            continue;
+                        }
+                        int64_t vi = (v[2] * G + v[1]) * G + v[0];
+                        double add = dens[i] * co.vol;
+#pragma omp atomic
+                        grid[vi] += add;
+                    }
+        }
+        free(cw.pl); free(cw.v); free(cw.tmp); free(cw.side);
+        free(cv.pl); free(cv.v); free(cv.tmp); free(cv.side);
+        free(f_nbr); free(f_shift); free(f_area); free(f_cen); free(f_dist); free(cb.c);
+    }
+    kd_free(&tree);
+    free(leaf_of);
+    const double vv = h[0] * h[1] * h[2];
+    for (int64_t v = 0; v < G3; v++) grid[v] /= vv;
+    counters[0] += tot_pred; counters[1] += tot_exact; counters[2] += tot_zero; counters[3] += tot_err;
+    return first_err;
 }
 
 int oracle_abi_version(void) { return 1; }

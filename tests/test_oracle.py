@@ -333,6 +333,35 @@ def test_green_gauss_gradient_periodic_lattice_zero(oracle_mod):
     assert np.abs(g).max() < 1e-6 * dens.max()
 
 
+@pytest.mark.parametrize("periodic", [True, False])
+def test_grid_volume_partition_of_unity(oracle_mod, periodic):
+    """The cells tile every voxel: with unit densities every voxel average is 1."""
+    x = inputs.uniform(500, seed=3)
+    g = oracle_mod.grid_volume_density(x, np.ones(len(x)), 0.0, 1.0, 5, periodic=periodic)
+    assert np.abs(g - 1.0).max() < 1e-12
+
+
+def test_grid_volume_mass_and_single_voxel(oracle_mod):
+    x = inputs.uniform(500, seed=3)
+    r = oracle_mod.cells(x, 0.0, 1.0, True, mode="certified")
+    d = np.random.default_rng(1).random(len(x))
+    mass = (d * r["vol"]).sum()
+    g = oracle_mod.grid_volume_density(x, d, 0.0, 1.0, 4)
+    assert abs(g.sum() / 64 - mass) < 1e-12 * mass  # sum of averages x voxel volume = total mass
+    g1 = oracle_mod.grid_volume_density(x, d, 0.0, 1.0, 1)
+    assert abs(g1.ravel()[0] - mass) < 1e-12 * mass  # one voxel: the box
+
+
+def test_grid_volume_lattice_cells_are_voxels(oracle_mod):
+    """SC lattice with one site per voxel: each voxel is exactly one cell (its walls lie on the cell faces,
+    a degenerate case for the exact predicates), so each voxel takes its site's density."""
+    x = inputs.sc_lattice(4)
+    d = np.arange(len(x), dtype=np.float64)
+    g = oracle_mod.grid_volume_density(x, d, 0.0, 1.0, 4)
+    a = np.floor(x * 4).astype(int)
+    assert np.abs(g[a[:, 2], a[:, 1], a[:, 0]] - d).max() < 1e-12
+
+
 def test_grid_nearest_matches_kdtree(oracle_mod):
     scipy_spatial = pytest.importorskip("scipy.spatial")
     x = inputs.uniform(300, seed=4)
