@@ -94,6 +94,7 @@ typedef struct vt_stats {
                                  [2] candidates collected */
     int64_t n_handed_over;    /* FP32 filter: cells the thread-per-cell kernel handed to the warp-per-cell kernel */
     int64_t n_bucket_passes;  /* FP32 filter: radius passes of the thread-per-cell kernel, summed over buckets */
+    int64_t n_grid_failed;    /* cell/voxel parts the last vt_grid_density_volume could not compute (0 normally) */
 } vt_stats;
 
 typedef struct vt_handle_s *vt_handle;
@@ -248,6 +249,21 @@ int vt_gradient_gg(vt_handle h, void *grad);
  * VT_ERR_UNSUPPORTED on a vt_build_batched handle.
  */
 int vt_grid_density(vt_handle h, int G, int S, void *grid);
+
+/*
+ * vt_grid_density_volume -- densities on a regular G^3 grid over the box as
+ * volume-weighted averages of the cell densities (Implementation section,
+ * "average Voronoi densities on a regular grid", read exactly):
+ *   grid[v] = sum_i rho_i |V_i intersect voxel v| / |voxel v|,
+ * voxel (a, b, c) = [lo + a L/G, lo + (a+1) L/G] per axis (x fastest in grid,
+ * device [G][G][G], dtype of pos); periodic boxes wrap.  Each cell is rebuilt
+ * from its facet planes and clipped by the walls of every voxel it meets, in
+ * FP32 (volumes to about 1e-6 relative).  1 <= G <= 1024.  Allocates, on the
+ * first call (and for a larger G), an FP64 accumulator of G^3 and a retry
+ * list; parts that cannot be computed are counted in vt_stats.n_grid_failed.
+ * VT_ERR_UNSUPPORTED on a vt_build_batched handle.
+ */
+int vt_grid_density_volume(vt_handle h, int G, void *grid);
 
 /*
  * vt_moments -- first and second moments of every cell (no counterpart in the paper; they define the

@@ -42,7 +42,7 @@ class vt_stats(ctypes.Structure):
                 ("n_exact_zero", ctypes.c_int64), ("max_faces", ctypes.c_int64), ("device_error", ctypes.c_int32),
                 ("error_particle", ctypes.c_int32), ("n_launches", ctypes.c_int64), ("t_sort_ms", ctypes.c_double),
                 ("t_clip_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 3), ("n_handed_over", ctypes.c_int64),
-                ("n_bucket_passes", ctypes.c_int64)]
+                ("n_bucket_passes", ctypes.c_int64), ("n_grid_failed", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -102,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_gradient_gg.restype = i32
     lib.vt_grid_density.argtypes = [P, i32, i32, P]
     lib.vt_grid_density.restype = i32
+    lib.vt_grid_density_volume.argtypes = [P, i32, P]
+    lib.vt_grid_density_volume.restype = i32
     lib.vt_moments.argtypes = [P, P, P]
     lib.vt_moments.restype = i32
     lib.vt_backward.argtypes = [P, P, ctypes.c_double, P]
@@ -336,6 +338,18 @@ def vt_gradient_gg(h: Handle, grad) -> None:
 
 def vt_grid_density(h: Handle, G: int, S: int, grid) -> None:
     _check(load_library().vt_grid_density(h.ptr, int(G), int(S), _ptr(grid)), "vt_grid_density")
+
+
+def vt_grid_density_volume(h: Handle, G: int, grid) -> None:
+    _check(load_library().vt_grid_density_volume(h.ptr, int(G), _ptr(grid)), "vt_grid_density_volume")
+
+
+def grid_density_volume(h: Handle, G: int):
+    import torch
+
+    g = torch.empty(G, G, G, dtype=h.dtype, device=h.device)
+    vt_grid_density_volume(h, G, g)
+    return g
 
 
 def vt_moments(h: Handle, centroid=None, energy=None) -> None:

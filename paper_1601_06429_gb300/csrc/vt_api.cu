@@ -15,6 +15,7 @@ using namespace vt;
 namespace {
 
 constexpr int RC_POOL_HOST = 1001;  // device code for "facet pool too small" (the host grows it)
+constexpr unsigned GRID_RETRY_CAP = 1u << 20;  // (cell, voxel) pairs of the volume-averaged grid's second pass
 
 // internal detail of the last failed vt_build on this thread (diagnostics)
 thread_local int g_last_detail = 0;
@@ -42,7 +43,7 @@ void free_handle(vt_handle h) {
     void* ptrs[] = {h->spos, h->perm, h->inv, h->tree_mem, h->cell, h->face_start, h->face_count, h->cstat,
                     h->exact_list, h->dens_sorted, h->faces, h->xws, h->tmp, h->nbr_off_cache, h->dstat,
                     h->keys, h->keys_alt, h->vals_alt, h->cnt_in, h->sset, h->sgeo, h->soff, h->set_in, h->warp_list,
-                    h->set_cfg};
+                    h->set_cfg, h->gacc, h->gretry, h->gcnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h;
@@ -560,6 +561,35 @@ int vt_grid_density(vt_handle h, int G, int S, void* grid) {
     return cuda_rc(cudaGetLastError());
 }
 
+int vt_grid_density_volume(vt_handle h, int G, void* grid) {
+    if (!h || !grid || G < 1 || G > 1024) return VT_ERR_INVALID;
+    if (h->n_sets > 0) return VT_ERR_UNSUPPORTED;  // a grid needs one box
+    int rc = ensure_density(h);
+    if (rc) return rc;
+    const int64_t n = (int64_t)G * G * G;
+    if (h->gacc_n < n) {
+        if (h->gacc) cudaFree(h->gacc);
+        h->gacc = nullptr;
+        h->gacc_n = 0;
+        if (cudaMalloc((void**)&h->gacc, n * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return VT_ERR_OOM;
+        }
+        h->gacc_n = n;
+    }
+    if (!h->gretry) {
+        if (cudaMalloc((void**)&h->gretry, (size_t)GRID_RETRY_CAP * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc((void**)&h->gcnt, 16 * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            return VT_ERR_OOM;
+        }
+    }
+    h->n_launches += launch_grid_volume(h->spos, h->dtype, h->N, h->geo, h->faces, h->face_start, h->face_count,
+                                        h->dens_sorted, G, h->gacc, h->gretry, GRID_RETRY_CAP, h->gcnt, grid,
+                                        h->sm_count, h->stream);
+    return cuda_rc(cudaGetLastError());
+}
+
 int vt_moments(vt_handle h, void* centroid, void* energy) {
     if (!h || (!centroid && !energy)) return VT_ERR_INVALID;
     h->n_launches += launch_moments(h->cell, h->spos, h->dtype, h->perm, h->N, h->geo, centroid, energy, h->stream);
@@ -600,6 +630,11 @@ int vt_status(vt_handle h, vt_stats* out) {
     out->reserved[1] = (int64_t)d.n_collect;
     out->reserved[2] = (int64_t)d.n_collected;
     out->n_handed_over = (int64_t)d.n_warp_cells;
+    if (h->gcnt) {
+        unsigned gc[2] = {0u, 0u};
+        if (cudaMemcpy(gc, h->gcnt, sizeof(gc), cudaMemcpyDeviceToHost) == cudaSuccess) out->n_grid_failed = gc[1];
+        else cudaGetLastError();
+    }
     out->n_bucket_passes = (int64_t)d.n_bucket_passes;
     out->error_particle = -1;
     if (d.error && d.error_cell >= 0 && d.error_cell < h->N) {

@@ -248,7 +248,7 @@ __device__ __forceinline__ void make_vertex(CT ax, CT ay, CT az, CT ah, CT an, C
     vx = wx * inv; vy = wy * inv; vz = wz * inv;
     CT vn = sqrt(f_fma<CT>(vz, vz, f_fma<CT>(vy, vy, vx * vx)));
     CT S = bn * cn + cn * an + an * bn;
-    CT H = ah + bh + ch;
+    CT H = fabs(ah) + fabs(bh) + fabs(ch);  // offsets are >= 0 except for the voxel walls of the grid average
     CT P = an * bn * cn;
     CT ad = fabs(det) - (CT)6 * u * P;
     if (!(ad > (CT)32 * u * P)) {

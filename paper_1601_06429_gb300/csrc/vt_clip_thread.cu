@@ -16,6 +16,8 @@
 // larger than its capacities, a start box that was too small, a duplicate point, or a security radius beyond
 // the passes it makes -- goes to a list that the warp kernel then takes (and from there, if needed, the exact
 // kernel).  Every decision this kernel takes is certified, so both kernels produce the same cells.
+#include <climits>
+
 #include "vt_clip_impl.cuh"
 
 namespace vt {
@@ -23,7 +25,6 @@ namespace {
 
 constexpr int TT = 64;        // triangles (cell vertices) per cell
 constexpr int TPL = 40;       // planes per cell: the six start walls and the cuts
-constexpr int TRM = 32;       // triangles removed by one cut
 constexpr int TCH = 256;      // points per chunk
 constexpr int TSTK = 256;     // traversal stack entries per warp
 constexpr int TWARPS = 4;     // warps per block
@@ -33,17 +34,21 @@ constexpr int TMAXPTS = 16384;  // points streamed per bucket before the remaini
 // lane-local cell.  V: vertex (x, y, z) relative to the site and its error bound; Tr: three 8-bit plane ids;
 // Pl: plane (n, h); Pn: |n|; Ps / Pc: the plane's source (sorted index, or the bits of an artificial wall's h)
 // and code (periodic image 0..26, box wall 27+w, artificial wall 33+w).
-struct TCell {
-    float4 V[TT];
-    uint32_t Tr[TT];
-    float4 Pl[TPL];
-    float Pn[TPL];
-    uint32_t Ps[TPL];
-    uint8_t Pc[TPL];
+template <int NT, int NP>
+struct TCellT {
+    static constexpr int MT = NT, MP = NP;  // capacities: triangles (a multiple of 32), planes (at most 255)
+    float4 V[NT];
+    uint32_t Tr[NT];
+    float4 Pl[NP];
+    float Pn[NP];
+    uint32_t Ps[NP];
+    uint8_t Pc[NP];
     int nT, nP;
     float R2;          // >= the squared distance of every exact vertex
     float bmin[3], bmax[3];
 };
+typedef TCellT<TT, TPL> TCell;       // the clipping kernel's cell
+typedef TCellT<128, 96> TCellBig;   // grid averages of cells beyond it
 
 struct TSmem {
     float4 chunk[TCH];     // x, y, z, sorted index (bits)
@@ -59,7 +64,8 @@ __device__ __forceinline__ void tri_ids(uint32_t t, uint32_t& a, uint32_t& b, ui
     a = t & 255u; b = (t >> 8) & 255u; c = (t >> 16) & 255u;
 }
 
-__device__ __forceinline__ bool vertex_of(const TCell& C, uint32_t a, uint32_t b, uint32_t c, float4& v) {
+template <class CL>
+__device__ __forceinline__ bool vertex_of(const CL& C, uint32_t a, uint32_t b, uint32_t c, float4& v) {
     const float4 A = C.Pl[a], B = C.Pl[b], Cc = C.Pl[c];
     float vx, vy, vz, ev, rr;
     make_vertex<float>(A.x, A.y, A.z, A.w, C.Pn[a], B.x, B.y, B.z, B.w, C.Pn[b], Cc.x, Cc.y, Cc.z, Cc.w, C.Pn[c],
@@ -69,7 +75,8 @@ __device__ __forceinline__ bool vertex_of(const TCell& C, uint32_t a, uint32_t b
 }
 
 // R2 and the outward-rounded box of the exact vertices
-__device__ void bound_cell(TCell& C) {
+template <class CL>
+__device__ void bound_cell(CL& C) {
     float r2 = 0.f, lo0 = 0.f, lo1 = 0.f, lo2 = 0.f, hi0 = 0.f, hi1 = 0.f, hi2 = 0.f;
     for (int t = 0; t < C.nT; t++) {
         const float4 v = C.V[t];
@@ -86,8 +93,8 @@ __device__ void bound_cell(TCell& C) {
 
 // Start polytope: the box of half-side B around the site (artificial walls), cut by the real box walls when
 // the set is bounded and a wall is closer.  Returns 0 or a failure code.
-template <typename P>
-__device__ int init_cell(TCell& C, const Geometry& g, const P& pi, uint32_t self, float B) {
+template <typename P, class CL>
+__device__ int init_cell(CL& C, const Geometry& g, const P& pi, uint32_t self, float B) {
     for (int w = 0; w < 6; w++) {
         const int axis = w >> 1;
         const bool upper = (w & 1) == 0;
@@ -126,17 +133,22 @@ __device__ int init_cell(TCell& C, const Geometry& g, const P& pi, uint32_t self
 }
 
 // Drop plane ids that no triangle uses (the start walls keep theirs).  Returns false if none is free.
-__device__ bool compact_planes(TCell& C) {
-    uint64_t used = 0x3full;
+template <class CL>
+__device__ bool compact_planes(CL& C) {
+    uint32_t used[(CL::MP + 31) / 32];
+    for (int w = 0; w < (CL::MP + 31) / 32; w++) used[w] = 0u;
+    used[0] = 0x3fu;
     for (int t = 0; t < C.nT; t++) {
         uint32_t a, b, c;
         tri_ids(C.Tr[t], a, b, c);
-        used |= (1ull << a) | (1ull << b) | (1ull << c);
+        used[a >> 5] |= 1u << (a & 31);
+        used[b >> 5] |= 1u << (b & 31);
+        used[c >> 5] |= 1u << (c & 31);
     }
-    uint8_t map[TPL];
+    uint8_t map[CL::MP];
     int n = 0;
     for (int p = 0; p < C.nP; p++) {
-        if ((used >> p) & 1ull) {
+        if ((used[p >> 5] >> (p & 31)) & 1u) {
             if (n != p) {
                 C.Pl[n] = C.Pl[p]; C.Pn[n] = C.Pn[p]; C.Ps[n] = C.Ps[p]; C.Pc[n] = C.Pc[p];
             }
@@ -157,28 +169,29 @@ __device__ bool compact_planes(TCell& C) {
 // triangle whose reverse y->x is in no removed triangle lies on the boundary of the removed region (its
 // neighbour across is kept) and becomes the new triangle (x, y, p).  New triangles fill the removed slots; the
 // array is then compacted.  Returns 0 or a failure code.
-__device__ int cut_cell(TCell& C, const unsigned* bm, float nx, float ny, float nz, float h, float nrm, uint32_t src,
+template <class CL>
+__device__ int cut_cell(CL& C, const unsigned* bm, float nx, float ny, float nz, float h, float nrm, uint32_t src,
                         int code) {
-    if (C.nP >= TPL && !compact_planes(C)) return TF_CAP_PLANES;
+    if (C.nP >= CL::MP && !compact_planes(C)) return TF_CAP_PLANES;
     const uint32_t p = (uint32_t)C.nP++;
     C.Pl[p] = make_float4(nx, ny, nz, h);
     C.Pn[p] = nrm;
     C.Ps[p] = src;
     C.Pc[p] = (uint8_t)code;
-    uint8_t rem[TRM];
-    uint32_t rtri[TRM];
+    uint8_t rem[CL::MT];
+    uint32_t rtri[CL::MT];
     int r = 0;
-    for (int w = 0; w < TT / 32; w++) {
+    for (int w = 0; w < CL::MT / 32; w++) {
         unsigned m = bm[w];
         while (m) {
             const int t = w * 32 + __ffs(m) - 1;
             m &= m - 1;
-            if (r == TRM) return TF_CAP_CUT;
+            if (r == CL::MT) return TF_CAP_CUT;
             rtri[r] = C.Tr[t];
             rem[r++] = (uint8_t)t;
         }
     }
-    uint8_t bx[TRM + 2], by[TRM + 2];
+    uint8_t bx[CL::MT + 2], by[CL::MT + 2];
     int nb = 0;
     for (int k = 0; k < r; k++) {
         uint32_t id[3];
@@ -193,7 +206,7 @@ __device__ int cut_cell(TCell& C, const unsigned* bm, float nx, float ny, float 
                 inner = (a == y && b == x) || (b == y && c == x) || (c == y && a == x);
             }
             if (!inner) {
-                if (nb == TRM + 2) return TF_CAP_CUT;
+                if (nb == CL::MT + 2) return TF_CAP_CUT;
                 bx[nb] = (uint8_t)x;
                 by[nb] = (uint8_t)y;
                 nb++;
@@ -201,7 +214,7 @@ __device__ int cut_cell(TCell& C, const unsigned* bm, float nx, float ny, float 
         }
     }
     if (nb < 3) return TF_CAP_CUT;
-    if (C.nT - r + nb > TT) return TF_CAP;
+    if (C.nT - r + nb > CL::MT) return TF_CAP;
     for (int i = 0; i < nb; i++) {
         const int slot = i < r ? (int)rem[i] : C.nT + (i - r);
         const uint32_t t = (uint32_t)bx[i] | ((uint32_t)by[i] << 8) | (p << 16);
@@ -215,7 +228,8 @@ __device__ int cut_cell(TCell& C, const unsigned* bm, float nx, float ny, float 
     } else {
         // holes rem[nb..r) (ascending): move the last live triangles into those below the new count
         const int n2 = C.nT - (r - nb);
-        unsigned hm[TT / 32] = {0u, 0u};
+        unsigned hm[CL::MT / 32];
+        for (int w = 0; w < CL::MT / 32; w++) hm[w] = 0u;
         for (int i = nb; i < r; i++) hm[rem[i] >> 5] |= 1u << (rem[i] & 31);
         int top = C.nT - 1;
         for (int i = nb; i < r; i++) {
@@ -232,10 +246,10 @@ __device__ int cut_cell(TCell& C, const unsigned* bm, float nx, float ny, float 
 }
 
 // n.v - h against the error bound for every vertex: beyond -> bm, undecided -> um
-__device__ __forceinline__ void test_plane(const TCell& C, float nx, float ny, float nz, float h, float nrm, float hb,
+template <class CL>
+__device__ __forceinline__ void test_plane(const CL& C, float nx, float ny, float nz, float h, float nrm, float hb,
                                            unsigned* bm, unsigned* um) {
-    bm[0] = bm[1] = 0u;
-    um[0] = um[1] = 0u;
+    for (int w = 0; w < CL::MT / 32; w++) bm[w] = um[w] = 0u;
     for (int t = 0; t < C.nT; t++) {
         const float4 v = C.V[t];
         const float s = __fmaf_rn(nx, v.x, __fmaf_rn(ny, v.y, __fmaf_rn(nz, v.z, -h)));
@@ -835,7 +849,278 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
     }
 }
 
+// ------------------------------------------------------------------ volume-averaged grid densities
+// Volume of a (closed, convex) lane-local polytope, by the divergence theorem from the site (which need not lie
+// inside): sum over planes of (signed offset / |n|) x area / 3.  A face is convex, so its vertices (the triangles
+// that list the plane) are ordered by angle about their mean in the plane's own basis; the polygon area then
+// needs nothing from the triangulation's adjacency, which a near-degenerate cut can leave inconsistent.
+template <class CL>
+__device__ float cell_volume(const CL& C) {
+    float vol = 0.f;
+    for (int p = 0; p < C.nP; p++) {
+        float ang[CL::MT];
+        uint8_t ft[CL::MT];
+        int m = 0;
+        float cx = 0.f, cy = 0.f, cz = 0.f;
+        for (int t = 0; t < C.nT; t++) {
+            uint32_t a, b, c;
+            tri_ids(C.Tr[t], a, b, c);
+            if (a != (uint32_t)p && b != (uint32_t)p && c != (uint32_t)p) continue;
+            ft[m++] = (uint8_t)t;
+            cx += C.V[t].x; cy += C.V[t].y; cz += C.V[t].z;
+        }
+        if (m < 3) continue;  // a plane that only touches the polytope: no area
+        const float im = 1.f / (float)m;
+        cx *= im; cy *= im; cz *= im;
+        const float4 pl = C.Pl[p];
+        const float inrm = 1.f / C.Pn[p];
+        const float nx = pl.x * inrm, ny = pl.y * inrm, nz = pl.z * inrm;
+        // u perpendicular to n, w = n x u
+        float ux, uy, uz;
+        if (fabsf(nx) < 0.9f) { ux = 0.f; uy = nz; uz = -ny; }
+        else { ux = -nz; uy = 0.f; uz = nx; }
+        const float iu = rsqrtf(ux * ux + uy * uy + uz * uz);
+        ux *= iu; uy *= iu; uz *= iu;
+        const float wx = ny * uz - nz * uy, wy = nz * ux - nx * uz, wz = nx * uy - ny * ux;
+        for (int k = 0; k < m; k++) {
+            const float4 v = C.V[ft[k]];
+            const float dx = v.x - cx, dy = v.y - cy, dz = v.z - cz;
+            ang[k] = atan2f(dx * wx + dy * wy + dz * wz, dx * ux + dy * uy + dz * uz);
+        }
+        for (int k = 1; k < m; k++) {  // insertion sort by angle
+            const float a = ang[k];
+            const uint8_t t = ft[k];
+            int q = k - 1;
+            while (q >= 0 && ang[q] > a) { ang[q + 1] = ang[q]; ft[q + 1] = ft[q]; q--; }
+            ang[q + 1] = a;
+            ft[q + 1] = t;
+        }
+        float area = 0.f;
+        for (int k = 0; k < m; k++) {
+            const float4 v1 = C.V[ft[k]], v2 = C.V[ft[k + 1 < m ? k + 1 : 0]];
+            const float ax = v1.x - cx, ay = v1.y - cy, az = v1.z - cz;
+            const float bx = v2.x - cx, by = v2.y - cy, bz = v2.z - cz;
+            area += 0.5f * ((ay * bz - az * by) * nx + (az * bx - ax * bz) * ny + (ax * by - ay * bx) * nz);
+        }
+        vol += pl.w * inrm * area * (float)(1.0 / 3.0);
+    }
+    return vol;
+}
+
+// Cut C by n.y <= h for a volume: a vertex is removed when n.v - h > 0 in FP32 (no error bound: an
+// ill-conditioned vertex has a wide bound that would keep a part the plane should remove, while a wrong sign on
+// a vertex within rounding of the plane changes the volume by a rounding-sized sliver).  Returns 1 if C became
+// empty, 0 otherwise, or a failure code (negative).
+template <class CL>
+__device__ int cut_plain(CL& C, float nx, float ny, float nz, float h, float nrm) {
+    const float u = Prec<float>::u();
+    unsigned bm[CL::MT / 32], um[CL::MT / 32];
+    (void)u;
+    test_plane(C, nx, ny, nz, h, 0.f, 0.f, bm, um);
+    int nb = 0;
+    for (int w = 0; w < CL::MT / 32; w++) nb += __popc(bm[w]);
+    if (nb == 0) return 0;
+    if (nb == C.nT) return 1;
+    const int f = cut_cell(C, bm, nx, ny, nz, h, nrm, 0u, CODE_ART);
+    return f ? -f : 0;
+}
+
+struct GridArgs {
+    const void* spos;
+    int64_t N;
+    Geometry geo;
+    const Face* faces;
+    const uint32_t* face_start;
+    const uint16_t* face_count;
+    const double* dens;  // sorted order
+    int G;
+    double h[3];         // voxel side L / G
+    double* acc;         // [G^3] sum of rho |cell & voxel|
+    int4* retry;         // (cell, voxel x, y, z unwrapped; x = INT_MIN: every voxel) for the larger cell type
+    unsigned retry_cap;
+    unsigned* n_retry;
+    unsigned* n_fail;
+};
+
+// The cell of sorted particle k from its facet planes (start: a cube of half-side lmin/4, which holds every cell
+// the build accepted, or the box walls).  Returns 0 or a failure code.
+template <typename P, class CL>
+__device__ int grid_cell(CL& C, const GridArgs& A, int64_t k, const P& pi) {
+    const Geometry& g = A.geo;
+    const double lmin = fmin(g.L[0], fmin(g.L[1], g.L[2]));
+    const float B = g.periodic ? (float)(0.25 * lmin) : (float)(2.0 * fmax(g.L[0], fmax(g.L[1], g.L[2])));
+    int f = init_cell<P>(C, g, pi, (uint32_t)k, B);
+    const uint32_t st = A.face_start[k];
+    const int cnt = A.face_count[k];
+    for (int q = 0; q < cnt && !f; q++) {
+        const Face fc = A.faces[st + q];
+        const float d2 = __fmaf_rn(fc.dz, fc.dz, __fmaf_rn(fc.dy, fc.dy, fc.dx * fc.dx));
+        const int r = cut_plain(C, fc.dx, fc.dy, fc.dz, 0.5f * d2, sqrtf(d2));
+        if (r) f = r < 0 ? -r : TF_CAP;  // a facet plane never empties its own cell
+    }
+    if (!f) bound_cell(C);
+    return f;
+}
+
+// Volume of cell C inside voxel (ax, ay, az) (unwrapped indices; periodic boxes wrap them), translated by `shift`
+// along every axis, into *vol; the voxel's linear index into *vi.  Returns 0, or a failure code; *vol = 0 when they
+// do not meet.
+template <class CL>
+__device__ int voxel_part(const CL& C, CL& D, const GridArgs& A, const double* xi, int64_t ax, int64_t ay, int64_t az,
+                          double shift, float* vol, int64_t* vi) {
+    const Geometry& g = A.geo;
+    const int64_t ia[3] = {ax, ay, az};
+    int64_t v[3];
+    double lo_[3], hi_[3];
+    for (int c = 0; c < 3; c++) {
+        int64_t q = ia[c] % A.G;
+        if (q < 0) q += A.G;
+        v[c] = q;
+        const double sl = (double)((ia[c] - q) / A.G) * g.L[c];
+        lo_[c] = g.lo[c] + (double)q * A.h[c] + sl - xi[c] + shift;
+        hi_[c] = g.lo[c] + (double)(q + 1) * A.h[c] + sl - xi[c] + shift;
+    }
+    *vi = (v[2] * A.G + v[1]) * A.G + v[0];
+    *vol = 0.f;
+    if (lo_[0] > C.bmax[0] || hi_[0] < C.bmin[0] || lo_[1] > C.bmax[1] || hi_[1] < C.bmin[1] || lo_[2] > C.bmax[2] ||
+        hi_[2] < C.bmin[2])
+        return 0;
+    D.nT = C.nT;
+    D.nP = C.nP;
+    for (int t = 0; t < C.nT; t++) { D.V[t] = C.V[t]; D.Tr[t] = C.Tr[t]; }
+    for (int p = 0; p < C.nP; p++) { D.Pl[p] = C.Pl[p]; D.Pn[p] = C.Pn[p]; D.Ps[p] = C.Ps[p]; D.Pc[p] = C.Pc[p]; }
+    for (int w = 0; w < 6; w++) {
+        const int axis = w >> 1;
+        const bool upper = (w & 1) == 0;
+        const float sg = upper ? 1.f : -1.f;
+        const float hh = upper ? (float)hi_[axis] : (float)(-lo_[axis]);
+        const int r = cut_plain(D, axis == 0 ? sg : 0.f, axis == 1 ? sg : 0.f, axis == 2 ? sg : 0.f, hh, 1.f);
+        if (r < 0) return -r;
+        if (r) return 0;  // empty
+    }
+    const float vv = cell_volume(D);
+    // a sliver's FP32 volume may come out slightly below zero; anything beyond 1e-5 of the voxel is a failure
+    if (vv < -1e-5f * (float)(A.h[0] * A.h[1] * A.h[2])) return 10;
+    *vol = fmaxf(vv, 0.f);
+    return 0;
+}
+
+// The retry pass's part: unshifted first; a voxel wall that passes within the rounding bound of a cell vertex
+// can make the kept and removed vertices of a cut inconsistent (the face splits), so the voxel is then
+// translated by 1e-5 and 4e-5 of its side (the part's volume moves by at most that slab: far below FP32
+// tolerance on the average) before giving up.
+template <class CL>
+__device__ int voxel_part_retry(const CL& C, CL& D, const GridArgs& A, const double* xi, int64_t ax, int64_t ay,
+                                int64_t az, float* vol, int64_t* vi) {
+    const double hmin = fmin(A.h[0], fmin(A.h[1], A.h[2]));
+    int e = voxel_part(C, D, A, xi, ax, ay, az, 0.0, vol, vi);
+    if (e) e = voxel_part(C, D, A, xi, ax, ay, az, 1e-5 * hmin, vol, vi);
+    if (e) e = voxel_part(C, D, A, xi, ax, ay, az, -4e-5 * hmin, vol, vi);
+    return e;
+}
+
+// a part that cannot be computed: counted in total and by reason (counters[4 + code])
+__device__ __forceinline__ void grid_fail(const GridArgs& A, int code) {
+    atomicAdd(A.n_fail, 1u);
+    atomicAdd(A.n_fail + 3 + (code > 0 && code < 12 ? code : 0), 1u);
+}
+
+__device__ __forceinline__ void push_retry(const GridArgs& A, int64_t k, int ax, int ay, int az) {
+    const unsigned slot = atomicAdd(A.n_retry, 1u);
+    if (slot < A.retry_cap) A.retry[slot] = make_int4((int)k, ax, ay, az);
+    else grid_fail(A, 11);
+}
+
+// One thread per cell (RETRY = false) or per retry entry (RETRY = true, the larger cell type): rho times the
+// volume of the cell inside each voxel its box meets is added to that voxel.  A pair the small cell type
+// cannot hold goes to the retry list, so that no voxel receives a part twice.
+template <typename P, class CL, bool RETRY>
+__global__ void __launch_bounds__(128) k_grid_volume(GridArgs A) {
+    const int64_t n = RETRY ? (int64_t)min(*((volatile unsigned*)A.n_retry), A.retry_cap) : A.N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        int4 ent = make_int4(0, INT_MIN, 0, 0);
+        if (RETRY) ent = A.retry[e];
+        const int64_t k = RETRY ? (int64_t)ent.x : e;
+        const P pi = ((const P*)A.spos)[k];
+        CL C, D;
+        int f = grid_cell<P, CL>(C, A, k, pi);
+        if (f) {
+            if (!RETRY) push_retry(A, k, INT_MIN, 0, 0);
+            else grid_fail(A, f);
+            continue;
+        }
+        const double xi[3] = {(double)pi.x, (double)pi.y, (double)pi.z};
+        const double rho = A.dens[k];
+        if (RETRY && ent.y != INT_MIN) {
+            float vol;
+            int64_t vi;
+            const int e2 = voxel_part_retry(C, D, A, xi, ent.y, ent.z, ent.w, &vol, &vi);
+            if (e2) grid_fail(A, e2);
+            else if (vol > 0.f) atomicAdd(&A.acc[vi], rho * (double)vol);
+            continue;
+        }
+        const Geometry& g = A.geo;
+        int64_t a0[3], a1[3];
+        for (int c = 0; c < 3; c++) {
+            a0[c] = (int64_t)floor((xi[c] + (double)C.bmin[c] - g.lo[c]) / A.h[c]) - 1;
+            a1[c] = (int64_t)floor((xi[c] + (double)C.bmax[c] - g.lo[c]) / A.h[c]) + 1;
+            if (!g.periodic) {
+                a0[c] = a0[c] < 0 ? 0 : a0[c];
+                a1[c] = a1[c] > A.G - 1 ? A.G - 1 : a1[c];
+            }
+        }
+        for (int64_t az = a0[2]; az <= a1[2]; az++)
+            for (int64_t ay = a0[1]; ay <= a1[1]; ay++)
+                for (int64_t ax = a0[0]; ax <= a1[0]; ax++) {
+                    float vol;
+                    int64_t vi;
+                    const int e2 = RETRY ? voxel_part_retry(C, D, A, xi, ax, ay, az, &vol, &vi)
+                                         : voxel_part(C, D, A, xi, ax, ay, az, 0.0, &vol, &vi);
+                    if (e2) {
+                        if (!RETRY) push_retry(A, k, (int)ax, (int)ay, (int)az);
+                        else grid_fail(A, e2);
+                    } else if (vol > 0.f) {
+                        atomicAdd(&A.acc[vi], rho * (double)vol);
+                    }
+                }
+    }
+}
+
+template <typename T>
+__global__ void k_grid_finish(const double* __restrict__ acc, int64_t n, double inv_vox, T* __restrict__ out) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) out[v] = (T)(acc[v] * inv_vox);
+}
+
 }  // namespace
+
+int launch_grid_volume(const void* spos, int dtype, int64_t N, const Geometry& g, const Face* faces,
+                       const uint32_t* face_start, const uint16_t* face_count, const double* dens_sorted, int G,
+                       double* acc, int4* retry, unsigned retry_cap, unsigned* counters, void* out, int sm_count,
+                       cudaStream_t s) {
+    GridArgs a;
+    a.spos = spos; a.N = N; a.geo = g; a.faces = faces; a.face_start = face_start; a.face_count = face_count;
+    a.dens = dens_sorted; a.G = G; a.acc = acc; a.retry = retry; a.retry_cap = retry_cap;
+    a.n_retry = counters; a.n_fail = counters + 1;
+    for (int c = 0; c < 3; c++) a.h[c] = g.L[c] / G;
+    const int64_t n = (int64_t)G * G * G;
+    cudaMemsetAsync(acc, 0, n * sizeof(double), s);
+    cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned), s);
+    const unsigned nb = (unsigned)((N + 127) / 128);
+    const unsigned rb = (unsigned)(sm_count * 4);
+    if (dtype == VT_F32) {
+        k_grid_volume<float4, TCell, false><<<nb, 128, 0, s>>>(a);
+        k_grid_volume<float4, TCellBig, true><<<rb, 128, 0, s>>>(a);
+    } else {
+        k_grid_volume<dpt4, TCell, false><<<nb, 128, 0, s>>>(a);
+        k_grid_volume<dpt4, TCellBig, true><<<rb, 128, 0, s>>>(a);
+    }
+    const double inv = 1.0 / (a.h[0] * a.h[1] * a.h[2]);
+    const unsigned gb = (unsigned)((n + 255) / 256);
+    if (dtype == VT_F32) k_grid_finish<float><<<gb, 256, 0, s>>>(acc, n, inv, (float*)out);
+    else k_grid_finish<double><<<gb, 256, 0, s>>>(acc, n, inv, (double*)out);
+    return 3;
+}
 
 int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s) {
     static int per_sm_dev[2][64] = {{0}};

@@ -129,6 +129,11 @@ struct vt_handle_s {
     vt::DevStatus hstat;    // host copy after build
     int64_t n_faces;
     int faces_on_device;    // set by vt_rebuild: the facet count is read from the device from then on
+    // volume-averaged grid: accumulator, retry list of the larger cell type, counters (retries, failures)
+    double* gacc;
+    int64_t gacc_n;
+    int4* gretry;
+    unsigned* gcnt;         // [16]: retries, failures, -, by reason (4 + code)
     int sm_count;
     int64_t n_launches;
     double t_sort_ms, t_clip_ms;

@@ -187,6 +187,38 @@ def test_green_gauss_gradient_of_a_linear_density(oracle_mod):
     assert np.abs(got[interior] - g_true[None, :]).max() < 1e-3
 
 
+# ---------------------------------------------------------------- volume-averaged grid
+@pytest.mark.parametrize("prec", ["plain64", "filter32"])
+def test_grid_volume_matches_oracle(uniform4096, oracle_mod, prec):
+    x, o = uniform4096
+    h = vt.vt_build(torch.from_numpy(x).cuda(), None, (0.0,) * 3, (1.0,) * 3, True, prec)
+    got = vt.grid_density_volume(h, 16).double().cpu().numpy()
+    assert vt.vt_status(h)["n_grid_failed"] == 0
+    ref = oracle_mod.grid_volume_density(x, 1.0 / o["vol"], 0.0, 1.0, 16)
+    assert np.abs(got - ref).max() <= 2e-5 * ref.max()
+
+
+def test_grid_volume_partition_of_unity_and_bounded(oracle_mod):
+    """Masses equal to the cell volumes make every density 1: every voxel average is then 1 (each voxel is
+    tiled by the cell parts, none counted twice); and a bounded halo set against the oracle."""
+    L = float(np.float32(31.5))
+    x = inputs.clustered(65536, L=L, seed=1)
+    pos = torch.from_numpy(x).cuda()
+    h = vt.vt_build(pos, None, (0.0,) * 3, (L,) * 3, True, "filter32")
+    vol, _, _ = vt.cells(h)
+    h2 = vt.vt_build(pos, vol.clone(), (0.0,) * 3, (L,) * 3, True, "filter32")
+    g = vt.grid_density_volume(h2, 32).double().cpu().numpy()
+    assert vt.vt_status(h2)["n_grid_failed"] == 0
+    assert np.abs(g - 1.0).max() < 2e-4
+    pts, off = inputs.halo_sets(n_sets=1, nmin=3000, nmax=3001, seed=6)
+    xb = pts[off[0]:off[1]].astype(np.float64)
+    o = oracle_mod.cells(xb, -1.0, 1.0, False, mode="certified")
+    hb = vt.vt_build(torch.from_numpy(xb).cuda(), None, (-1.0,) * 3, (1.0,) * 3, False, "plain64")
+    got = vt.grid_density_volume(hb, 12).double().cpu().numpy()
+    ref = oracle_mod.grid_volume_density(xb, 1.0 / o["vol"], -1.0, 1.0, 12, periodic=False)
+    assert np.abs(got - ref).max() <= 1e-5 * ref.max()
+
+
 # ---------------------------------------------------------------- bounded box
 def test_bounded_halo_sets(oracle_mod):
     pts, off = inputs.halo_sets(n_sets=3, nmin=300, nmax=5000, seed=6, dtype=np.float32)
