@@ -52,7 +52,7 @@ WORK = {
 }
 # DRAM bytes (read + write) of one launch of the clipping kernel, from one ncu capture of this kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/launches_clustered16M.md)
-CLIP_TRAFFIC = {("clustered16M", "filter32"): 10.488e9}
+CLIP_TRAFFIC = {("clustered16M", "filter32"): 10.480e9}
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
 
