@@ -56,7 +56,7 @@ def _load():
         P = ctypes.c_void_p
         i64 = ctypes.c_int64
         i32 = ctypes.c_int
-        lib.oracle_cells.argtypes = [i64, P, P, P, i32, P, i64, i32, i32] + [P] * 15 + [i32]
+        lib.oracle_cells.argtypes = [i64, P, P, P, i32, P, i64, i32, i32] + [P] * 16 + [i32]
         lib.oracle_cells.restype = i32
         lib.oracle_insphere_side.argtypes = [P, P, P, P, P, i32]
         lib.oracle_insphere_side.restype = i32
@@ -93,7 +93,8 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     ``nedge``, ``ntest`` (planes examined) and ``ncut`` (planes that cut),
     the faces in CSR form (``face_off``, ``f_nbr`` (neighbour id, -1-w for
     box wall w), ``f_shift`` (periodic image), ``f_area``, ``f_cen``,
-    ``f_dist``), and ``counters`` = (predicates, exact fallbacks, exact
+    ``f_dist``, ``f_m3`` = integral of |y - x_i|^2 (y - x_i) over the facet), and ``counters`` = (predicates,
+    exact fallbacks, exact
     zeros, failed cells).
     """
     lib = _load()
@@ -120,12 +121,13 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     f_area = np.zeros(n * face_cap)
     f_cen = np.zeros((n * face_cap, 3))
     f_dist = np.zeros(n * face_cap)
+    f_m3 = np.zeros((n * face_cap, 3))
     counters = np.zeros(4, np.int64)
     rc = lib.oracle_cells(N, _ptr(pos), _ptr(lo), _ptr(hi), int(bool(periodic)), _ptr(wh), n,
                           {"brute": 0, "certified": 1}[mode], face_cap,
                           _ptr(vol), _ptr(cen), _ptr(mom2), _ptr(rmax), _ptr(nface), _ptr(nvert), _ptr(nedge),
                           _ptr(ntest), _ptr(ncut), _ptr(f_nbr), _ptr(f_shift), _ptr(f_area), _ptr(f_cen),
-                          _ptr(f_dist), _ptr(counters), int(nthreads))
+                          _ptr(f_dist), _ptr(f_m3), _ptr(counters), int(nthreads))
     if rc != 0:
         raise RuntimeError("oracle_cells failed with code %d on %d cell(s)" % (rc, int(counters[3])))
     nf = nface.astype(np.int64)
@@ -135,7 +137,7 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     return dict(which=wh if wh is not None else np.arange(N, dtype=np.int64), vol=vol, cen=cen, mom2=mom2, rmax=rmax,
                 nface=nface, nvert=nvert, nedge=nedge, ntest=ntest, ncut=ncut, face_off=face_off,
                 f_nbr=f_nbr[sel], f_shift=f_shift[sel], f_area=f_area[sel], f_cen=f_cen[sel],
-                f_dist=f_dist[sel], counters=counters)
+                f_dist=f_dist[sel], f_m3=f_m3[sel], counters=counters)
 
 
 def neighbours(res, self_ids=None):
@@ -227,6 +229,29 @@ def gradient_green_gauss(res, pos, dens_self, dens_all, box_lo=0.0, box_hi=1.0):
     g = np.zeros((n, 3))
     np.add.at(g, owner, w[:, None] * c)
     return g / res["vol"][:, None]
+
+
+def cvt_weighted_gradient(res, pos, w, box_lo=0.0, box_hi=1.0):
+    """Gradient of the weighted centroidal energy E_w = sum_i w_i integral over V_i of |y - x_i|^2 with respect to
+    every listed site (all particles must be listed).  Moving x_k changes cell k's integrand, 2 w_k V_k (x_k - z_k),
+    and moves each facet f between k and j along its normal by (y - x_k).delta / |d_f| at facet point y; since
+    |y - x_k| = |y - x_j| on the facet, the energy densities on its two sides differ by (w_k - w_j) |y - x_k|^2, so
+    dE_w/dx_k = 2 w_k V_k (x_k - z_k) + sum_f (w_k - w_j) / |d_f| integral_f |y - x_k|^2 (y - x_k) dA.
+    Box walls do not move.  ``w`` indexes by particle id."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    w = np.asarray(w, dtype=np.float64)
+    wh = res["which"]
+    assert len(wh) == len(pos)
+    own = 2.0 * (w[wh] * res["vol"])[:, None] * (pos[wh] - res["cen"])
+    off = res["face_off"]
+    owner = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    j = res["f_nbr"]
+    inner = j >= 0
+    wj = np.where(inner, w[np.where(inner, j, 0)], 0.0)
+    coef = np.where(inner, (w[wh[owner]] - wj) / np.where(inner, 2.0 * res["f_dist"], 1.0), 0.0)
+    g = own.copy()
+    np.add.at(g, owner, coef[:, None] * res["f_m3"])
+    return g
 
 
 def grid_nearest(pos, box_lo, box_hi, G, S=1, periodic=True, nthreads=0):

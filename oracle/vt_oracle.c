@@ -728,8 +728,27 @@ static int run_certified(cellwork *cw, const kdtree *t, candbuf *cb, int64_t lea
 }
 
 /* faces and moments of the final polytope */
+/* cubic face moment over a triangle: integral of |y|^2 y dA by the degree-3 rule of Strang and Fix
+ * (weight -27/48 at the centroid, 25/48 at the three points with barycentric coordinates (3/5, 1/5, 1/5)),
+ * exact for cubic integrands; returns the integral divided by the triangle's area */
+static void tri_m3(const double *y0, const double *y1, const double *y2, double *out) {
+    double p[4][3];
+    for (int c = 0; c < 3; c++) {
+        p[0][c] = (y0[c] + y1[c] + y2[c]) / 3.0;
+        p[1][c] = 0.6 * y0[c] + 0.2 * y1[c] + 0.2 * y2[c];
+        p[2][c] = 0.2 * y0[c] + 0.6 * y1[c] + 0.2 * y2[c];
+        p[3][c] = 0.2 * y0[c] + 0.2 * y1[c] + 0.6 * y2[c];
+    }
+    const double w[4] = {-27.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0};
+    for (int c = 0; c < 3; c++) out[c] = 0.0;
+    for (int k = 0; k < 4; k++) {
+        double r2 = p[k][0] * p[k][0] + p[k][1] * p[k][1] + p[k][2] * p[k][2];
+        for (int c = 0; c < 3; c++) out[c] += w[k] * r2 * p[k][c];
+    }
+}
+
 static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int32_t *f_shift, double *f_area,
-                   double *f_cen, double *f_dist) {
+                   double *f_cen, double *f_dist, double *f_m3) {
     const problem *pb = cw->pb;
     int *vlist = (int *)malloc(sizeof(int) * (cw->nv + 1));
     int *order = (int *)malloc(sizeof(int) * (cw->nv + 1));
@@ -773,7 +792,7 @@ static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int3
         double nn = sqrt(P->n[0] * P->n[0] + P->n[1] * P->n[1] + P->n[2] * P->n[2]);
         double nh[3] = {P->n[0] / nn, P->n[1] / nn, P->n[2] / nn};
         const double *y0 = cw->v[order[0]].y;
-        double A = 0.0, C[3] = {0, 0, 0}, fv = 0.0, fz[3] = {0, 0, 0}, fm2 = 0.0;
+        double A = 0.0, C[3] = {0, 0, 0}, fv = 0.0, fz[3] = {0, 0, 0}, fm2 = 0.0, M3[3] = {0, 0, 0};
         for (int k = 1; k + 1 < cnt; k++) {
             const double *y1 = cw->v[order[k]].y, *y2 = cw->v[order[k + 1]].y;
             double e1[3] = {y1[0] - y0[0], y1[1] - y0[1], y1[2] - y0[2]};
@@ -782,6 +801,9 @@ static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int3
             double at = 0.5 * (cr[0] * nh[0] + cr[1] * nh[1] + cr[2] * nh[2]);
             A += at;
             for (int c = 0; c < 3; c++) C[c] += at * (y0[c] + y1[c] + y2[c]) / 3.0;
+            double t3[3];
+            tri_m3(y0, y1, y2, t3);
+            for (int c = 0; c < 3; c++) M3[c] += at * t3[c];
             /* tetrahedron (site, y0, y1, y2), signed like the fan triangle */
             double tv = (y0[0] * (y1[1] * y2[2] - y1[2] * y2[1]) - y0[1] * (y1[0] * y2[2] - y1[2] * y2[0]) +
                          y0[2] * (y1[0] * y2[1] - y1[1] * y2[0])) / 6.0;
@@ -808,6 +830,7 @@ static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int3
         }
         f_area[nf] = A;
         f_dist[nf] = P->h / nn;
+        if (f_m3) for (int c = 0; c < 3; c++) f_m3[3 * nf + c] = sg * M3[c];
         nf++;
     }
     co->vol = vol;
@@ -842,7 +865,8 @@ static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int3
  *   examined), ncut[k] (planes that cut);
  * face slots [k*face_cap, k*face_cap + nface[k]):  f_nbr (neighbour id, or
  *   -1-w for box wall w), f_shift[3] (image shift), f_area, f_cen[3]
- *   (absolute), f_dist (distance from x_i to the facet plane).
+ *   (absolute), f_dist (distance from x_i to the facet plane), f_m3[3] (NULL: not
+ *   wanted) = integral over the facet of |y - x_i|^2 (y - x_i) dA.
  * counters[0..3] += predicates, exact fallbacks, exact zeros, errors.
  * Returns 0, or the first per-cell error code.
  */
@@ -851,7 +875,7 @@ int oracle_cells(int64_t N, const double *pos, const double *box_lo, const doubl
                  double *mom2, double *rmax, int32_t *nface, int32_t *nvert, int32_t *nedge, int64_t *ntest,
                  int64_t *ncut,
                  int64_t *f_nbr, int32_t *f_shift, double *f_area, double *f_cen, double *f_dist,
-                 int64_t *counters, int nthreads) {
+                 double *f_m3, int64_t *counters, int nthreads) {
     problem pb;
     pb.N = N; pb.x = pos; pb.periodic = periodic;
     for (int c = 0; c < 3; c++) { pb.lo[c] = box_lo[c]; pb.hi[c] = box_hi[c]; pb.L[c] = box_hi[c] - box_lo[c]; }
@@ -889,7 +913,8 @@ int oracle_cells(int64_t N, const double *pos, const double *box_lo, const doubl
             memset(&co, 0, sizeof(co));
             if (rc == 0)
                 rc = extract(&cw, &co, face_cap, f_nbr + k * face_cap, f_shift + 3 * k * face_cap,
-                             f_area + k * face_cap, f_cen + 3 * k * face_cap, f_dist + k * face_cap);
+                             f_area + k * face_cap, f_cen + 3 * k * face_cap, f_dist + k * face_cap,
+                             f_m3 ? f_m3 + 3 * k * face_cap : NULL);
             tot_pred += cw.n_pred; tot_exact += cw.n_exact; tot_zero += cw.n_zero;
             ntest[k] = cw.n_tested; ncut[k] = cw.n_cut;
             if (rc != 0) {
@@ -1119,7 +1144,7 @@ int oracle_grid_volume(int64_t N, const double *pos, const double *box_lo, const
                         if (cv.nv == 0) continue;
                         cellout co;
                         memset(&co, 0, sizeof(co));
-                        int e = extract(&cv, &co, MAXP, f_nbr, f_shift, f_area, f_cen, f_dist);
+                        int e = extract(&cv, &co, MAXP, f_nbr, f_shift, f_area, f_cen, f_dist, NULL);
                         if (e) {
                             tot_err++;
 #pragma omp critical

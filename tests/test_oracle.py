@@ -362,6 +362,39 @@ def test_grid_volume_lattice_cells_are_voxels(oracle_mod):
     assert np.abs(g[a[:, 2], a[:, 1], a[:, 0]] - d).max() < 1e-12
 
 
+def test_face_cubic_moment_of_a_cube(oracle_mod):
+    """Closed form: a face of the cube of side a (SC lattice) at distance a/2 has
+    integral |y|^2 y dA = (a/2)(a^4/4 + a^4/6) = 5 a^5 / 24 along its normal, zero across."""
+    x = inputs.sc_lattice(4)
+    r = oracle_mod.cells(x, 0.0, 1.0, True, mode="brute")
+    a = 0.25
+    n = (r["f_cen"][:6] - x[0]) / (a / 2)
+    assert np.abs(r["f_m3"][:6] - 5 * a ** 5 / 24 * n).max() < 1e-12
+
+
+def test_weighted_cvt_gradient_finite_differences(oracle_mod):
+    """dE_w/dx against central differences of E_w = sum_i w_i E_i (the oracle's cell second moments)."""
+    x = inputs.uniform(300, seed=5)
+    w = np.random.default_rng(2).random(300) + 0.5
+    r = oracle_mod.cells(x, 0.0, 1.0, True, mode="certified")
+    g = oracle_mod.cvt_weighted_gradient(r, x, w)
+
+    def E(xx):
+        return float((w * oracle_mod.cells(xx % 1.0, 0.0, 1.0, True, mode="certified")["mom2"]).sum())
+
+    for k in (3, 77, 150):
+        for c in range(3):
+            xp = x.copy()
+            xm = x.copy()
+            xp[k, c] += 1e-5
+            xm[k, c] -= 1e-5
+            fd = (E(xp) - E(xm)) / 2e-5
+            assert abs(fd - g[k, c]) <= 1e-6 * np.abs(g[k]).max(), (k, c, fd, g[k, c])
+    # equal weights: the facet terms cancel and the gradient is the centroidal one, 2 w V (x - z)
+    g1 = oracle_mod.cvt_weighted_gradient(r, x, np.full(300, 2.0))
+    assert np.allclose(g1, 4.0 * r["vol"][:, None] * (x - r["cen"]), rtol=0, atol=1e-15)
+
+
 def test_grid_nearest_matches_kdtree(oracle_mod):
     scipy_spatial = pytest.importorskip("scipy.spatial")
     x = inputs.uniform(300, seed=4)
