@@ -266,6 +266,23 @@ int vt_grid_density(vt_handle h, int G, int S, void *grid);
 int vt_grid_density_volume(vt_handle h, int G, void *grid);
 
 /*
+ * vt_backward_weighted -- gradient of the weighted centroidal energy
+ *   E_w = sum_i w_i integral over V_i of |y - x_i|^2
+ * (the paper has no counterpart; the unweighted form is vt_backward's energy
+ * term): moving x_k changes cell k's integrand and moves each facet between k
+ * and a neighbour j, across which the energy density jumps by
+ * (w_k - w_j) |y - x_k|^2, so
+ *   dE_w/dx_k = 2 w_k V_k (x_k - z_k)
+ *             + sum_j (w_k - w_j) / |x_j - x_k| integral_f |y - x_k|^2 (y - x_k) dA.
+ *   w        device [N] weights, input order, dtype of pos
+ *   dE_dpos  device [N][3] out, input order
+ * Each cell is rebuilt from its facet planes in FP32 and the facet integrals
+ * taken with an exact cubic triangle rule.  Cells that cannot be rebuilt are
+ * counted in vt_stats.n_grid_failed (their rows are then not written).
+ */
+int vt_backward_weighted(vt_handle h, const void *w, void *dE_dpos);
+
+/*
  * vt_moments -- first and second moments of every cell (no counterpart in the paper; they define the
  * centroidal Voronoi energy used with vt_backward).
  *   centroid  device [N][3] or NULL: the cell's centroid, in the frame of the positions (wrapped into

@@ -104,6 +104,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_grid_density.restype = i32
     lib.vt_grid_density_volume.argtypes = [P, i32, P]
     lib.vt_grid_density_volume.restype = i32
+    lib.vt_backward_weighted.argtypes = [P, P, P]
+    lib.vt_backward_weighted.restype = i32
     lib.vt_moments.argtypes = [P, P, P]
     lib.vt_moments.restype = i32
     lib.vt_backward.argtypes = [P, P, ctypes.c_double, P]
@@ -350,6 +352,20 @@ def grid_density_volume(h: Handle, G: int):
     g = torch.empty(G, G, G, dtype=h.dtype, device=h.device)
     vt_grid_density_volume(h, G, g)
     return g
+
+
+def vt_backward_weighted(h: Handle, w, dE_dpos) -> None:
+    _check(load_library().vt_backward_weighted(h.ptr, _ptr(w), _ptr(dE_dpos)), "vt_backward_weighted")
+
+
+def backward_weighted(h: Handle, w):
+    """Gradient of sum_i w_i integral_{V_i} |y - x_i|^2 with respect to the positions, [N,3]."""
+    import torch
+
+    w = w.to(device=h.device, dtype=h.dtype).contiguous()
+    out = torch.empty(h.N, 3, dtype=h.dtype, device=h.device)
+    vt_backward_weighted(h, w, out)
+    return out
 
 
 def vt_moments(h: Handle, centroid=None, energy=None) -> None:

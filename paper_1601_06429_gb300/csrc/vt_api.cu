@@ -561,6 +561,28 @@ int vt_grid_density(vt_handle h, int G, int S, void* grid) {
     return cuda_rc(cudaGetLastError());
 }
 
+namespace {
+int ensure_retry(vt_handle h) {
+    if (h->gretry) return VT_OK;
+    if (cudaMalloc((void**)&h->gretry, (size_t)GRID_RETRY_CAP * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc((void**)&h->gcnt, 16 * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_OOM;
+    }
+    return VT_OK;
+}
+}  // namespace
+
+int vt_backward_weighted(vt_handle h, const void* w, void* dE_dpos) {
+    if (!h || !w || !dE_dpos) return VT_ERR_INVALID;
+    int rc = ensure_retry(h);
+    if (rc) return rc;
+    h->n_launches += launch_cvt_weighted(h->spos, h->dtype, h->N, h->geo, h->faces, h->face_start, h->face_count,
+                                         h->cell, h->perm, w, dE_dpos, h->gretry, GRID_RETRY_CAP, h->gcnt, h->sm_count,
+                                         h->stream);
+    return cuda_rc(cudaGetLastError());
+}
+
 int vt_grid_density_volume(vt_handle h, int G, void* grid) {
     if (!h || !grid || G < 1 || G > 1024) return VT_ERR_INVALID;
     if (h->n_sets > 0) return VT_ERR_UNSUPPORTED;  // a grid needs one box
@@ -577,13 +599,8 @@ int vt_grid_density_volume(vt_handle h, int G, void* grid) {
         }
         h->gacc_n = n;
     }
-    if (!h->gretry) {
-        if (cudaMalloc((void**)&h->gretry, (size_t)GRID_RETRY_CAP * sizeof(int4)) != cudaSuccess ||
-            cudaMalloc((void**)&h->gcnt, 16 * sizeof(unsigned)) != cudaSuccess) {
-            cudaGetLastError();
-            return VT_ERR_OOM;
-        }
-    }
+    rc = ensure_retry(h);
+    if (rc) return rc;
     h->n_launches += launch_grid_volume(h->spos, h->dtype, h->N, h->geo, h->faces, h->face_start, h->face_count,
                                         h->dens_sorted, G, h->gacc, h->gretry, GRID_RETRY_CAP, h->gcnt, grid,
                                         h->sm_count, h->stream);

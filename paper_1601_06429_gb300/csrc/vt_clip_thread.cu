@@ -912,7 +912,8 @@ __device__ float cell_volume(const CL& C) {
 // a vertex within rounding of the plane changes the volume by a rounding-sized sliver).  Returns 1 if C became
 // empty, 0 otherwise, or a failure code (negative).
 template <class CL>
-__device__ int cut_plain(CL& C, float nx, float ny, float nz, float h, float nrm) {
+__device__ int cut_plain(CL& C, float nx, float ny, float nz, float h, float nrm, uint32_t src = 0u,
+                         int code = CODE_ART) {
     const float u = Prec<float>::u();
     unsigned bm[CL::MT / 32], um[CL::MT / 32];
     (void)u;
@@ -921,7 +922,7 @@ __device__ int cut_plain(CL& C, float nx, float ny, float nz, float h, float nrm
     for (int w = 0; w < CL::MT / 32; w++) nb += __popc(bm[w]);
     if (nb == 0) return 0;
     if (nb == C.nT) return 1;
-    const int f = cut_cell(C, bm, nx, ny, nz, h, nrm, 0u, CODE_ART);
+    const int f = cut_cell(C, bm, nx, ny, nz, h, nrm, src, code);
     return f ? -f : 0;
 }
 
@@ -955,7 +956,8 @@ __device__ int grid_cell(CL& C, const GridArgs& A, int64_t k, const P& pi) {
     for (int q = 0; q < cnt && !f; q++) {
         const Face fc = A.faces[st + q];
         const float d2 = __fmaf_rn(fc.dz, fc.dz, __fmaf_rn(fc.dy, fc.dy, fc.dx * fc.dx));
-        const int r = cut_plain(C, fc.dx, fc.dy, fc.dz, 0.5f * d2, sqrtf(d2));
+        // the plane keeps its neighbour's sorted index (code 0: a plane between particles)
+        const int r = cut_plain(C, fc.dx, fc.dy, fc.dz, 0.5f * d2, sqrtf(d2), fc.nbr, 0);
         if (r) f = r < 0 ? -r : TF_CAP;  // a facet plane never empties its own cell
     }
     if (!f) bound_cell(C);
@@ -1086,6 +1088,134 @@ __global__ void __launch_bounds__(128) k_grid_volume(GridArgs A) {
     }
 }
 
+// ------------------------------------------------------------------ weighted centroidal energy gradient
+// integral of |y|^2 y over the triangle (a, b, c) divided by its area: the degree-3 rule of Strang and Fix
+// (weight -27/48 at the centroid, 25/48 at barycentric (3/5, 1/5, 1/5) and its permutations), exact for cubics
+__device__ __forceinline__ void tri_m3(float4 a, float4 b, float4 c, float* out) {
+    const float w0 = -27.f / 48.f, w1 = 25.f / 48.f;
+    float px[4], py[4], pz[4];
+    px[0] = (a.x + b.x + c.x) * (1.f / 3.f); py[0] = (a.y + b.y + c.y) * (1.f / 3.f); pz[0] = (a.z + b.z + c.z) * (1.f / 3.f);
+    px[1] = 0.6f * a.x + 0.2f * b.x + 0.2f * c.x; py[1] = 0.6f * a.y + 0.2f * b.y + 0.2f * c.y; pz[1] = 0.6f * a.z + 0.2f * b.z + 0.2f * c.z;
+    px[2] = 0.2f * a.x + 0.6f * b.x + 0.2f * c.x; py[2] = 0.2f * a.y + 0.6f * b.y + 0.2f * c.y; pz[2] = 0.2f * a.z + 0.6f * b.z + 0.2f * c.z;
+    px[3] = 0.2f * a.x + 0.2f * b.x + 0.6f * c.x; py[3] = 0.2f * a.y + 0.2f * b.y + 0.6f * c.y; pz[3] = 0.2f * a.z + 0.2f * b.z + 0.6f * c.z;
+    out[0] = out[1] = out[2] = 0.f;
+    for (int k = 0; k < 4; k++) {
+        const float w = (k == 0 ? w0 : w1) * (px[k] * px[k] + py[k] * py[k] + pz[k] * pz[k]);
+        out[0] += w * px[k]; out[1] += w * py[k]; out[2] += w * pz[k];
+    }
+}
+
+struct CvtArgs {
+    const void* spos;
+    int64_t N;
+    Geometry geo;
+    const Face* faces;
+    const uint32_t* face_start;
+    const uint16_t* face_count;
+    const CellOut* cell;
+    const uint32_t* perm;
+    const void* w;        // weights, input order, dtype of pos
+    int dtype;
+    void* out;            // dE_w / dx, input order [N][3]
+    int4* retry;
+    unsigned retry_cap;
+    unsigned* n_retry;
+    unsigned* n_fail;
+};
+
+// dE_w/dx_k = 2 w_k V_k (x_k - z_k) + sum over facets (w_k - w_j) / |d| integral_f |y - x_k|^2 (y - x_k) dA, one
+// thread per cell (RETRY: per listed cell, larger cell type); the facet integral over the facet polygon of the cell
+// rebuilt from its facet planes, vertices ordered by angle in the facet plane and fanned.
+template <typename P, class CL, bool RETRY>
+__global__ void __launch_bounds__(128) k_cvt_weighted(CvtArgs A) {
+    const int64_t n = RETRY ? (int64_t)min(*((volatile unsigned*)A.n_retry), A.retry_cap) : A.N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = RETRY ? (int64_t)A.retry[e].x : e;
+        const P pi = ((const P*)A.spos)[k];
+        GridArgs ga;
+        ga.geo = A.geo; ga.faces = A.faces; ga.face_start = A.face_start; ga.face_count = A.face_count;
+        CL C;
+        const int f = grid_cell<P, CL>(C, ga, k, pi);
+        if (f) {
+            if (!RETRY) {
+                const unsigned slot = atomicAdd(A.n_retry, 1u);
+                if (slot < A.retry_cap) A.retry[slot] = make_int4((int)k, 0, 0, 0);
+                else atomicAdd(A.n_fail, 1u);
+            } else {
+                atomicAdd(A.n_fail, 1u);
+            }
+            continue;
+        }
+        const uint32_t ik = A.perm[k];
+        const double wk = A.dtype == VT_F32 ? (double)((const float*)A.w)[ik] : ((const double*)A.w)[ik];
+        const CellOut co = A.cell[k];
+        double gx = -2.0 * wk * co.vol * co.zx, gy = -2.0 * wk * co.vol * co.zy, gz = -2.0 * wk * co.vol * co.zz;
+        for (int p = 6; p < C.nP; p++) {
+            if (C.Pc[p] >= 27) continue;
+            float ang[CL::MT];
+            uint8_t ft[CL::MT];
+            int m = 0;
+            float cx = 0.f, cy = 0.f, cz = 0.f;
+            for (int t = 0; t < C.nT; t++) {
+                uint32_t a, b, c;
+                tri_ids(C.Tr[t], a, b, c);
+                if (a != (uint32_t)p && b != (uint32_t)p && c != (uint32_t)p) continue;
+                ft[m++] = (uint8_t)t;
+                cx += C.V[t].x; cy += C.V[t].y; cz += C.V[t].z;
+            }
+            if (m < 3) continue;
+            const float im = 1.f / (float)m;
+            cx *= im; cy *= im; cz *= im;
+            const float4 pl = C.Pl[p];
+            const float inrm = 1.f / C.Pn[p];
+            const float nx = pl.x * inrm, ny = pl.y * inrm, nz = pl.z * inrm;
+            float ux, uy, uz;
+            if (fabsf(nx) < 0.9f) { ux = 0.f; uy = nz; uz = -ny; }
+            else { ux = -nz; uy = 0.f; uz = nx; }
+            const float iu = rsqrtf(ux * ux + uy * uy + uz * uz);
+            ux *= iu; uy *= iu; uz *= iu;
+            const float wx = ny * uz - nz * uy, wy = nz * ux - nx * uz, wz = nx * uy - ny * ux;
+            for (int q = 0; q < m; q++) {
+                const float4 v = C.V[ft[q]];
+                const float dx = v.x - cx, dy = v.y - cy, dz = v.z - cz;
+                ang[q] = atan2f(dx * wx + dy * wy + dz * wz, dx * ux + dy * uy + dz * uz);
+            }
+            for (int q = 1; q < m; q++) {
+                const float a = ang[q];
+                const uint8_t t = ft[q];
+                int r = q - 1;
+                while (r >= 0 && ang[r] > a) { ang[r + 1] = ang[r]; ft[r + 1] = ft[r]; r--; }
+                ang[r + 1] = a;
+                ft[r + 1] = t;
+            }
+            // fan from the first vertex: area along the outward normal times the rule's mean of |y|^2 y
+            double mx = 0.0, my = 0.0, mz = 0.0;
+            const float4 v0 = C.V[ft[0]];
+            for (int q = 1; q + 1 < m; q++) {
+                const float4 v1 = C.V[ft[q]], v2 = C.V[ft[q + 1]];
+                const float e1x = v1.x - v0.x, e1y = v1.y - v0.y, e1z = v1.z - v0.z;
+                const float e2x = v2.x - v0.x, e2y = v2.y - v0.y, e2z = v2.z - v0.z;
+                const float at = 0.5f * ((e1y * e2z - e1z * e2y) * nx + (e1z * e2x - e1x * e2z) * ny +
+                                         (e1x * e2y - e1y * e2x) * nz);
+                float t3[3];
+                tri_m3(v0, v1, v2, t3);
+                mx += (double)at * t3[0]; my += (double)at * t3[1]; mz += (double)at * t3[2];
+            }
+            const uint32_t ij = A.perm[C.Ps[p]];
+            const double wj = A.dtype == VT_F32 ? (double)((const float*)A.w)[ij] : ((const double*)A.w)[ij];
+            const double cf = (wk - wj) * (double)inrm;
+            gx += cf * mx; gy += cf * my; gz += cf * mz;
+        }
+        if (A.dtype == VT_F32) {
+            float* o = (float*)A.out + 3 * (int64_t)ik;
+            o[0] = (float)gx; o[1] = (float)gy; o[2] = (float)gz;
+        } else {
+            double* o = (double*)A.out + 3 * (int64_t)ik;
+            o[0] = gx; o[1] = gy; o[2] = gz;
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_grid_finish(const double* __restrict__ acc, int64_t n, double inv_vox, T* __restrict__ out) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1120,6 +1250,27 @@ int launch_grid_volume(const void* spos, int dtype, int64_t N, const Geometry& g
     if (dtype == VT_F32) k_grid_finish<float><<<gb, 256, 0, s>>>(acc, n, inv, (float*)out);
     else k_grid_finish<double><<<gb, 256, 0, s>>>(acc, n, inv, (double*)out);
     return 3;
+}
+
+int launch_cvt_weighted(const void* spos, int dtype, int64_t N, const Geometry& g, const Face* faces,
+                        const uint32_t* face_start, const uint16_t* face_count, const CellOut* cell,
+                        const uint32_t* perm, const void* w, void* out, int4* retry, unsigned retry_cap,
+                        unsigned* counters, int sm_count, cudaStream_t s) {
+    CvtArgs a;
+    a.spos = spos; a.N = N; a.geo = g; a.faces = faces; a.face_start = face_start; a.face_count = face_count;
+    a.cell = cell; a.perm = perm; a.w = w; a.dtype = dtype; a.out = out; a.retry = retry; a.retry_cap = retry_cap;
+    a.n_retry = counters; a.n_fail = counters + 1;
+    cudaMemsetAsync(counters, 0, 16 * sizeof(unsigned), s);
+    const unsigned nb = (unsigned)((N + 127) / 128);
+    const unsigned rb = (unsigned)(sm_count * 4);
+    if (dtype == VT_F32) {
+        k_cvt_weighted<float4, TCell, false><<<nb, 128, 0, s>>>(a);
+        k_cvt_weighted<float4, TCellBig, true><<<rb, 128, 0, s>>>(a);
+    } else {
+        k_cvt_weighted<dpt4, TCell, false><<<nb, 128, 0, s>>>(a);
+        k_cvt_weighted<dpt4, TCellBig, true><<<rb, 128, 0, s>>>(a);
+    }
+    return 2;
 }
 
 int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s) {

@@ -116,3 +116,20 @@ def test_lattice_is_a_lloyd_fixed_point():
     energy.sum().backward()
     step = x.grad / (2.0 * vol[:, None].detach())
     assert float(step.abs().max()) < 1e-5 * (1.0 / 16)
+
+
+def test_weighted_cvt_gradient_matches_oracle(oracle_mod):
+    """dE_w/dx for E_w = sum_i w_i E_i (per-cell weights) against the oracle, on 4096 uniform points (FP64 path),
+    and with equal weights against vt_backward's centroidal-energy term."""
+    x = inputs.uniform(4096, seed=0)
+    o = oracle_mod.cells(x, 0.0, 1.0, True, mode="certified")
+    w = np.random.default_rng(9).random(len(x)) + 0.5
+    ref = oracle_mod.cvt_weighted_gradient(o, x, w)
+    h = vt.vt_build(torch.from_numpy(x).cuda(), None, (0.0,) * 3, (1.0,) * 3, True, "plain64")
+    got = vt.backward_weighted(h, torch.from_numpy(w)).cpu().numpy()
+    assert vt.vt_status(h)["n_grid_failed"] == 0
+    scale = np.linalg.norm(ref, axis=1)
+    assert (np.linalg.norm(got - ref, axis=1) <= 1e-4 * scale + 1e-5 * scale.max()).all()
+    eq = vt.backward_weighted(h, torch.full((len(x),), 0.7, dtype=torch.float64)).cpu().numpy()
+    ref_eq = vt.backward(h, torch.zeros(len(x), dtype=torch.float64), 0.7).cpu().numpy()
+    assert np.abs(eq - ref_eq).max() <= 1e-6 * np.abs(ref_eq).max()
