@@ -69,3 +69,54 @@ def lloyd_step(pos, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), alpha=1.0, p
         y = torch.remainder(pos.detach() - step - lo, L) + lo
         y = torch.where(y >= hi, lo.expand_as(y), y)
     return y, float(E.detach())
+
+
+class LloydRunner:
+    """Repeated Lloyd steps on one handle: the tessellation of each new configuration goes through vt_rebuild
+    (no allocation, no synchronisation), and with ``graph=True`` the whole step (rebuild, moments, position
+    update) is captured once in a CUDA graph and replayed.  Positions stay on the device; ``step()`` returns
+    the total centroidal energy of the configuration it started from (a device scalar; ``float()`` syncs)."""
+
+    def __init__(self, pos, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), alpha=1.0, precision="filter32",
+                 graph=False):
+        self.stream = torch.cuda.Stream(device=pos.device)
+        self.x = pos.detach().clone().contiguous()
+        self.lo = torch.tensor(box_lo, dtype=pos.dtype, device=pos.device)
+        self.hi = torch.tensor(box_hi, dtype=pos.dtype, device=pos.device)
+        self.alpha = alpha
+        n = self.x.shape[0]
+        self.cen = torch.empty(n, 3, dtype=pos.dtype, device=pos.device)
+        self.energy = torch.empty(n, dtype=pos.dtype, device=pos.device)
+        self.E = torch.zeros((), dtype=torch.float64, device=pos.device)
+        torch.cuda.synchronize(pos.device)
+        with torch.cuda.stream(self.stream):
+            self.h = vt.vt_build(self.x, None, box_lo, box_hi, True, precision, stream=self.stream)
+            self._body()  # one untimed step outside any capture
+        self.stream.synchronize()
+        self.graph = None
+        if graph:
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=self.stream):
+                self._body()
+
+    def _body(self):
+        # Lloyd: x <- centroid of its cell (alpha = 1); centroid = x + (z - x), wrapped into the box
+        vt.vt_rebuild(self.h, self.x)
+        vt.vt_moments(self.h, self.cen, self.energy)
+        self.E.copy_(self.energy.sum(dtype=torch.float64))
+        L = self.hi - self.lo
+        d = torch.remainder(self.cen - self.x + 0.5 * L, L) - 0.5 * L  # minimum image of z - x
+        y = torch.remainder(self.x + self.alpha * d - self.lo, L) + self.lo
+        self.x.copy_(torch.where(y >= self.hi, self.lo.expand_as(y), y))
+
+    def step(self):
+        with torch.cuda.stream(self.stream):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._body()
+        torch.cuda.current_stream(self.x.device).wait_stream(self.stream)
+        return self.E
+
+    def status(self):
+        return vt.vt_status(self.h)
