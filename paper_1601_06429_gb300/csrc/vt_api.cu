@@ -174,6 +174,7 @@ int make_geometry(const double* lo, const double* hi, int periodic, int precisio
         geo.lo[c] = lo[c];
         geo.hi[c] = hi[c];
         geo.L[c] = hi[c] - lo[c];
+        geo.qs[c] = (float)(65536.0 / geo.L[c]);
         geo.Lf[c] = (float)geo.L[c];
         geo.halfLf[c] = 0.5f * geo.Lf[c];
         geo.lof[c] = (float)lo[c];
@@ -181,6 +182,9 @@ int make_geometry(const double* lo, const double* hi, int periodic, int precisio
         if (precision == VT_FILTER32 && periodic && (double)geo.Lf[c] != geo.L[c]) return VT_ERR_UNSUPPORTED;
     }
     geo.periodic = periodic ? 1 : 0;
+    geo.box_f32 = 1;
+    for (int c = 0; c < 3; c++)
+        if ((double)geo.lof[c] != geo.lo[c] || (double)geo.hif[c] != geo.hi[c]) geo.box_f32 = 0;
     return VT_OK;
 }
 

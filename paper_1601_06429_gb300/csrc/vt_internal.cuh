@@ -65,6 +65,8 @@ struct CellOut {
 
 struct Geometry {
     double lo[3], hi[3], L[3];
+    float qs[3];            // 65536 / L per axis: the Morton key's quantisation (FP32: the key only orders)
+    int box_f32;            // lo and hi are FP32 numbers: FP32 inputs can be checked against the box in FP32
     float Lf[3], halfLf[3], lof[3], hif[3];
     int periodic;
 };

@@ -92,6 +92,7 @@ extern "C" int vt_volumes_noalloc(const void* pos, int dtype, int64_t N, const d
         geo.lo[c] = box_lo[c];
         geo.hi[c] = box_hi[c];
         geo.L[c] = box_hi[c] - box_lo[c];
+        geo.qs[c] = (float)(65536.0 / geo.L[c]);
         geo.Lf[c] = (float)geo.L[c];
         geo.halfLf[c] = 0.5f * geo.Lf[c];
         geo.lof[c] = (float)box_lo[c];
@@ -99,6 +100,9 @@ extern "C" int vt_volumes_noalloc(const void* pos, int dtype, int64_t N, const d
         if (periodic && (double)geo.Lf[c] != geo.L[c]) return VT_ERR_UNSUPPORTED;
     }
     geo.periodic = periodic ? 1 : 0;
+    geo.box_f32 = 1;
+    for (int c = 0; c < 3; c++)
+        if ((double)geo.lof[c] != geo.lo[c] || (double)geo.hif[c] != geo.hi[c]) geo.box_f32 = 0;
     unsigned char* base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;

@@ -25,6 +25,18 @@ __device__ __forceinline__ uint64_t spread3_16(uint32_t v) {
     return x;
 }
 
+// x in the box: periodic [lo, hi), bounded [lo, hi]; false for NaN.  FP32 inputs against a box whose ends are
+// FP32 numbers compare exactly in FP32 (no FP64 on the path, which runs at 1/64 of the FP32 rate).
+template <typename T>
+__device__ __forceinline__ bool in_box(T x, const Geometry& g, int c) {
+    if (sizeof(T) == 4 && g.box_f32) {
+        const float xf = (float)x;
+        return g.periodic ? (xf >= g.lof[c] && xf < g.hif[c]) : (xf >= g.lof[c] && xf <= g.hif[c]);
+    }
+    const double xd = (double)x;
+    return g.periodic ? (xd >= g.lo[c] && xd < g.hi[c]) : (xd >= g.lo[c] && xd <= g.hi[c]);
+}
+
 template <typename T>
 __global__ void k_key(const T* __restrict__ pos, int64_t N, Geometry g, uint64_t* __restrict__ key,
                       uint32_t* __restrict__ idx, DevStatus* st) {
@@ -34,10 +46,11 @@ __global__ void k_key(const T* __restrict__ pos, int64_t N, Geometry g, uint64_t
     bool bad = false;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        double x = (double)pos[3 * i + c];
-        bool ok = g.periodic ? (x >= g.lo[c] && x < g.hi[c]) : (x >= g.lo[c] && x <= g.hi[c]);
+        const T x = pos[3 * i + c];
+        const bool ok = in_box<T>(x, g, c);
         if (!ok) bad = true;  // also catches NaN
-        double t = (x - g.lo[c]) / g.L[c] * 65536.0;
+        // the key only orders the particles: FP32 suffices (the index is clamped below)
+        const float t = ((float)x - g.lof[c]) * g.qs[c];
         int qi = ok ? (int)t : 0;
         q[c] = (uint32_t)min(max(qi, 0), 65535);
     }
@@ -62,10 +75,11 @@ __global__ void k_key_batched(const T* __restrict__ pos, int64_t N, const Geomet
     bool bad = false;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        double x = (double)pos[3 * i + c];
-        bool ok = g.periodic ? (x >= g.lo[c] && x < g.hi[c]) : (x >= g.lo[c] && x <= g.hi[c]);
+        const T x = pos[3 * i + c];
+        const bool ok = in_box<T>(x, g, c);
         if (!ok) bad = true;
-        double t = (x - g.lo[c]) / g.L[c] * 65536.0;
+        // the key only orders the particles: FP32 suffices (the index is clamped below)
+        const float t = ((float)x - g.lof[c]) * g.qs[c];
         int qi = ok ? (int)t : 0;
         q[c] = (uint32_t)min(max(qi, 0), 65535);
     }
