@@ -214,6 +214,7 @@ int scan_u16_i64(const uint16_t* in, int64_t* out, int64_t n, void* tmp, cudaStr
 constexpr int RS_WARPS = 8;
 constexpr int RS_ROUNDS = 16;
 constexpr int RS_TILE = RS_WARPS * RS_ROUNDS * 32;  // 4096
+constexpr int RS_SMEM = RS_TILE * (8 + 4);             // staged tile: keys and values
 
 __global__ void __launch_bounds__(256) k_radix_hist(const uint64_t* __restrict__ key, int64_t N, int shift,
                                                     uint32_t* __restrict__ hist, int nblocks) {
@@ -229,15 +230,25 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint64_t* __restrict__
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+// Scatter of one tile: every key's rank within its digit (per warp, then over the warps) gives its position in
+// the tile reordered by digit; the tile is staged in that order in shared memory and written out position by
+// position, so that consecutive threads write consecutive addresses of one digit's run (coalesced stores)
+// instead of up to 32 digit buckets per warp.  Dynamic shared memory: RS_TILE keys and values.
 __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t* __restrict__ key, const uint32_t* __restrict__ val,
                                                        uint64_t* __restrict__ key_out, uint32_t* __restrict__ val_out,
                                                        int64_t N, int shift, const uint32_t* __restrict__ goff,
                                                        int nblocks) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint64_t* skey = reinterpret_cast<uint64_t*>(rs_smem);
+    uint32_t* sval = reinterpret_cast<uint32_t*>(skey + RS_TILE);
     __shared__ uint32_t cnt[RS_WARPS][256];
+    __shared__ uint32_t boff[256];   // start of each digit in the reordered tile
+    __shared__ uint32_t wsum[RS_WARPS];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < RS_WARPS * 256; k += 256) (&cnt[0][0])[k] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * RS_ROUNDS * 32;
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    int64_t base = tile0 + (int64_t)w * RS_ROUNDS * 32;
     uint64_t kk[RS_ROUNDS];
     uint32_t vv[RS_ROUNDS];
     uint32_t rk[RS_ROUNDS];
@@ -258,27 +269,52 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t* __restric
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps, per digit
+    // per digit: exclusive prefix over the warps, and the digit's total in the tile
+    uint32_t total = 0;
     {
         int d = threadIdx.x;
-        uint32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < RS_WARPS; ww++) {
             uint32_t c = cnt[ww][d];
-            cnt[ww][d] = run;
-            run += c;
+            cnt[ww][d] = total;
+            total += c;
         }
     }
+    // exclusive scan of the digit totals over the block (thread d holds digit d)
+    {
+        uint32_t x = total;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        uint32_t add = 0;
+        for (int ww = 0; ww < w; ww++) add += wsum[ww];
+        boff[threadIdx.x] = add + x - total;
+    }
     __syncthreads();
+    // stage the tile in digit order
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; r++) {
         int64_t i = base + r * 32 + lane;
         if (i < N) {
             uint32_t d = (uint32_t)((kk[r] >> shift) & 255);
-            uint32_t p = goff[(int64_t)d * nblocks + blockIdx.x] + cnt[w][d] + rk[r];
-            key_out[p] = kk[r];
-            val_out[p] = vv[r];
+            uint32_t lp = boff[d] + cnt[w][d] + rk[r];
+            skey[lp] = kk[r];
+            sval[lp] = vv[r];
         }
+    }
+    __syncthreads();
+    // write out: position t of the reordered tile goes to its digit's run in the global order
+    const int n = (int)min((int64_t)RS_TILE, N - tile0);
+    for (int t = threadIdx.x; t < n; t += 256) {
+        const uint64_t k2 = skey[t];
+        const uint32_t d = (uint32_t)((k2 >> shift) & 255);
+        const uint32_t p = goff[(int64_t)d * nblocks + blockIdx.x] + ((uint32_t)t - boff[d]);
+        key_out[p] = k2;
+        val_out[p] = sval[t];
     }
 }
 
@@ -294,6 +330,14 @@ int radix_sort(uint64_t* key, uint32_t* val, uint64_t* key_alt, uint32_t* val_al
     int nb = (int)((N + RS_TILE - 1) / RS_TILE);
     if (nb == 0) return 0;
     int launches = 0;
+    // the staged scatter uses more than the default 48 KB of dynamic shared memory (set once per device)
+    static int smem_set[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+        cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+        smem_set[dev] = 1;
+    }
     uint32_t* hist = (uint32_t*)tmp;
     uint32_t* goff = hist + (size_t)nb * 256;
     void* stmp = goff + (size_t)nb * 256;
@@ -306,7 +350,7 @@ int radix_sort(uint64_t* key, uint32_t* val, uint64_t* key_alt, uint32_t* val_al
         int shift = 8 * p;
         k_radix_hist<<<nb, 256, 0, s>>>(ka, N, shift, hist, nb);
         launches += 2 + scan_u32_u32(hist, goff, (int64_t)nb * 256, stmp, s);
-        k_radix_scatter<<<nb, 256, 0, s>>>(ka, va, kb, vb, N, shift, goff, nb);
+        k_radix_scatter<<<nb, 256, RS_SMEM, s>>>(ka, va, kb, vb, N, shift, goff, nb);
         uint64_t* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
