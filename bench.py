@@ -40,9 +40,9 @@ METRIC = "Voronoi cells/sec (fwd, bwd) at 16.7M clustered pts on 1 GB300; roofli
 UNIT = "cells/s"
 
 # Algorithmic work of one cell, from the oracle on a 2048-cell sample of the workload (seed 7):
-# W = n_cert * V * 6 + V * 40 + F * 30 flops with n_cert the sites examined before the security stop,
-# V the vertices and F the facets of the final cell (see the design notes); bytes per cell of the
-# HBM-bound stages likewise.
+# W = n_cert * V * 6 + V * 40 + F * 30 flops with n_cert the sites examined before the security stop (every
+# one must be tested against the cell's vertices, 3 FMA each), V the vertices (a vertex from three planes costs
+# about 40 flops) and F the facets of the final cell (about 30 flops each for area, centroid and volume).
 WORK = {
     "clustered16M": {"n_cert": 163.2, "verts": 26.74, "faces": 15.37},
     "clustered2M": {"n_cert": 150.0, "verts": 26.7, "faces": 15.3},

@@ -9,7 +9,7 @@ Tolerances (per particle, max over the compared particles):
     (l_i = V_i^(1/3)); on the FP32 path the GPU densities themselves carry
     relative errors up to 2e-5, which the least-squares fit turns into an
     absolute gradient error of order 2e-5 * rho_i / l_i * k, so the floor is
-    raised to 1e-1 rho_i / l_i there (see the design notes);
+    raised to 1e-1 rho_i / l_i there;
   * grid: the nearest particle is decided in FP64 with the same evaluation
     order on both sides, so grid values are compared exactly.
 """
