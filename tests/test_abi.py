@@ -88,6 +88,61 @@ def test_build_rejects_bad_arguments_without_device_work(lib):
         binding.VT_ERR_UNSUPPORTED
 
 
+def test_batched_rejects_bad_sets_without_device_work(lib):
+    """vt_build_batched and vt_autotune_batched check set_off, n_sets, the boxes and the per-set parameters on the
+    host before they touch the device."""
+    h = ctypes.c_void_p(123)
+    fake = ctypes.c_void_p(16)
+    I64 = ctypes.c_int64 * 4
+    I32 = ctypes.c_int32 * 3
+    box = [0.0, 0.0, 0.0, 1.0, 1.0, 1.0]
+    boxes = (ctypes.c_double * 18)(*(box * 3))
+    good = I64(0, 5, 5, 9)
+    k_out, t_out = I32(), I32()
+
+    def batched(off, n, bx=boxes, dtype=0, set_k=None, set_tpc=None, p=None):
+        return lib.vt_build_batched(ctypes.byref(h), fake, dtype, None, off, n, bx, set_k, set_tpc,
+                                    ctypes.byref(p) if p is not None else None, None)
+
+    def tune(off, n, bx=boxes, dtype=0):
+        return lib.vt_autotune_batched(fake, dtype, off, n, bx, None, 0, k_out, t_out, None)
+
+    assert lib.vt_build_batched(None, fake, 0, None, good, 3, boxes, None, None, None, None) == binding.VT_ERR_INVALID
+    bad_cases = [
+        (I64(0, 5, 5, 9), 0),           # no sets
+        (I64(0, 5, 5, 9), 65537),       # more than VT_MAX_SETS
+        (I64(1, 5, 5, 9), 3),           # set_off[0] != 0
+        (I64(0, 5, 4, 9), 3),           # decreasing offsets
+        (I64(0, 0, 0, 0), 3),           # no points at all
+    ]
+    for off, n in bad_cases:
+        h.value = 123
+        assert batched(off, n) == binding.VT_ERR_INVALID, (list(off), n)
+        assert h.value is None
+        assert tune(off, n) == binding.VT_ERR_INVALID, (list(off), n)
+    assert batched(good, 3, dtype=7) == binding.VT_ERR_INVALID
+    assert tune(good, 3, dtype=7) == binding.VT_ERR_INVALID
+    flat = (ctypes.c_double * 18)(*(box * 2 + [0.0, 0.0, 0.0, 1.0, 0.0, 1.0]))  # set 2's box has no height
+    assert batched(good, 3, bx=flat) == binding.VT_ERR_INVALID
+    assert batched(good, 3, set_k=I32(24, 7, 24)) == binding.VT_ERR_INVALID        # k_target below 8
+    assert batched(good, 3, set_k=I32(24, 121, 24)) == binding.VT_ERR_INVALID      # k_target above 120
+    assert batched(good, 3, set_tpc=I32(32, 1, 4)) == binding.VT_ERR_INVALID       # only 1 or 32 threads per cell
+    p = binding.vt_default_params()
+    p.threads_per_cell = 2
+    assert batched(good, 3, p=p) == binding.VT_ERR_INVALID
+    assert lib.vt_autotune_batched(fake, 0, good, 3, boxes, None, 0, None, t_out, None) == binding.VT_ERR_INVALID
+
+
+def test_newer_calls_reject_null_arguments(lib):
+    fake = ctypes.c_void_p(16)
+    assert lib.vt_rebuild(None, fake, None) == binding.VT_ERR_INVALID
+    assert lib.vt_gradient_gg(None, fake) == binding.VT_ERR_INVALID
+    assert lib.vt_grid_density_volume(None, 8, fake) == binding.VT_ERR_INVALID
+    assert lib.vt_backward_weighted(None, fake, fake) == binding.VT_ERR_INVALID
+    assert lib.vt_moments(None, fake, fake) == binding.VT_ERR_INVALID
+    assert lib.vt_probe_fp32_tflops(None, None) == binding.VT_ERR_INVALID
+
+
 def test_calls_reject_null_handle(lib):
     assert lib.vt_cells(None, None, None, None, None) == binding.VT_ERR_INVALID
     assert lib.vt_density(None, None) == binding.VT_ERR_INVALID
