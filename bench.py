@@ -39,15 +39,16 @@ sys.path.insert(0, ROOT)
 METRIC = "Voronoi cells/sec (fwd, bwd) at 16.7M clustered pts on 1 GB300; roofline fraction"
 UNIT = "cells/s"
 
-# Algorithmic work of one cell, from the oracle on a 2048-cell sample of the workload (seed 7):
+# Algorithmic work of one cell, from the oracle on a 2048-cell sample of each workload (seed 7; the table is
+# the output of oracle/work_per_cell.py):
 # W = n_cert * V * 6 + V * 40 + F * 30 flops with n_cert the sites examined before the security stop (every
 # one must be tested against the cell's vertices, 3 FMA each), V the vertices (a vertex from three planes costs
 # about 40 flops) and F the facets of the final cell (about 30 flops each for area, centroid and volume).
 WORK = {
-    "clustered16M": {"n_cert": 163.2, "verts": 26.74, "faces": 15.37},
-    "clustered2M": {"n_cert": 150.0, "verts": 26.7, "faces": 15.3},
-    "clustered64k": {"n_cert": 175.8, "verts": 26.4, "faces": 15.2},
-    "uniform4096": {"n_cert": 42.4, "verts": 27.1, "faces": 15.56},
+    "uniform4096": {"n_cert": 42.75, "verts": 27.05, "faces": 15.53},
+    "clustered64k": {"n_cert": 177.45, "verts": 26.50, "faces": 15.25},
+    "clustered2M": {"n_cert": 213.01, "verts": 26.64, "faces": 15.32},
+    "clustered16M": {"n_cert": 163.17, "verts": 26.74, "faces": 15.37},
     "halosets4096": {"n_cert": 147.19, "verts": 26.55, "faces": 15.27},
 }
 # DRAM bytes (read + write) of one launch of the clipping kernel, from one ncu capture of this kernel

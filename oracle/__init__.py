@@ -3,6 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use this package.
 The GPU library never imports it, and it shares no code with the GPU path.
+``work_per_cell.py`` (run by hand, and by a test) prints the oracle's per-cell work counters that
+``bench.py`` keeps as its table of algorithmic flops per cell.
 
 What each function follows in the paper:
 

@@ -1,0 +1,37 @@
+"""Host-side parts of bench.py (no GPU): the algorithmic work table against the oracle's counters, and the
+flop and roofline arithmetic built on it."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_work_table_row_matches_the_oracle():
+    # the 4096-point row, re-derived from the oracle's counters on the same 2048-cell sample
+    from oracle import work_per_cell
+
+    c = work_per_cell.counters("uniform4096", 2048)
+    row = bench.WORK["uniform4096"]
+    for k in ("n_cert", "verts", "faces"):
+        assert abs(c[k] - row[k]) <= 0.005 + 1e-9, (k, c[k], row[k])
+
+
+def test_work_counters_match_poisson_means():
+    # uniform points: the final cells are Poisson-Voronoi cells, whose mean vertex and facet counts are
+    # 96 pi^2 / 35 and 2 + 48 pi^2 / 35 (Meijering); the 2048-cell sample is within a few standard errors
+    import math
+
+    row = bench.WORK["uniform4096"]
+    assert abs(row["verts"] - 96 * math.pi ** 2 / 35) < 0.3
+    assert abs(row["faces"] - (2 + 48 * math.pi ** 2 / 35)) < 0.15
+
+
+def test_flops_per_cell_formula():
+    w = {"n_cert": 10.0, "verts": 2.0, "faces": 3.0}
+    assert bench.flops_per_cell(w) == 10 * 2 * 6 + 2 * 40 + 3 * 30
+    assert bench.flops_per_cell(bench.WORK["clustered16M"]) == pytest.approx(27_700, rel=0.01)
