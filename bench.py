@@ -413,9 +413,7 @@ def run_ours(args):
     ids_h = torch.empty(ids.numel(), dtype=torch.int32).pin_memory()
     xd2 = torch.empty_like(xd)
 
-    def e2e_step():
-        xd2.copy_(xh, non_blocking=True)
-        n = step(xd2)
+    def copy_out(n):
         outs_h["vol"].copy_(vol, non_blocking=True)
         outs_h["dens"].copy_(dens, non_blocking=True)
         outs_h["grad"].copy_(grad, non_blocking=True)
@@ -424,9 +422,14 @@ def run_ours(args):
             outs_h["grid"].copy_(grid, non_blocking=True)
         outs_h["dpos"].copy_(dpos, non_blocking=True)
         ids_h[:n].copy_(ids[:n], non_blocking=True)
+
+    def e2e_step():
+        xd2.copy_(xh, non_blocking=True)
+        n = step(xd2)
+        copy_out(n)
         return n
 
-    e2e_step()
+    n = e2e_step()
     torch.cuda.synchronize()
     barrier(ws)
     e0.record(stream)
@@ -438,6 +441,14 @@ def run_ours(args):
     e2e_value = ws * N * args.steps / (te_ms / 1000.0)
     h2d = N * 12
     d2h = N * 4 + N * 4 + N * 12 + (N + 1) * 8 + G ** 3 * 4 + N * 12 + n * 4
+    # the same copies alone, on the same buffers and stream: the part of the e2e step that is host<->device
+    e0.record(stream)
+    for _ in range(args.steps):
+        xd2.copy_(xh, non_blocking=True)
+        copy_out(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = e0.elapsed_time(e1) / args.steps
 
     # ---------------- roofline of the clipping kernel (FP32 issue bound)
     wk = WORK.get(args.workload, WORK["clustered16M"])
@@ -464,6 +475,8 @@ def run_ours(args):
             "step_roofline": step_roofline(N, G, nnz / N, fpc, peak, fwd_ms + grid_ms + bwd_ms),
             "faces_per_cell": nnz / N,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e_copies": {"ms_per_step": copy_ms, "gb_per_s": (h2d + d2h) / (copy_ms * 1e6),
+                           "note": "the e2e step's copies alone, back to back (pinned host buffers, one stream)"},
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": CLIP_TRAFFIC.get((args.workload, args.precision)),
