@@ -35,3 +35,20 @@ def test_flops_per_cell_formula():
     w = {"n_cert": 10.0, "verts": 2.0, "faces": 3.0}
     assert bench.flops_per_cell(w) == 10 * 2 * 6 + 2 * 40 + 3 * 30
     assert bench.flops_per_cell(bench.WORK["clustered16M"]) == pytest.approx(27_700, rel=0.01)
+
+
+def test_step_roofline_takes_the_larger_bound_per_stage():
+    N, G, faces = 1000, 0, 15.0
+    clip_bytes = 32 * faces + 40
+    per_cell = 24 + 6 * 32 + 40 + clip_bytes + (36 * faces + 8) + 40 + (40 * faces + 12) + (36 * faces + 12)
+    ms_per_byte = 1e3 / (bench.HBM_GBS * 1e9)
+    # clipping bound by its flops: the clipping bytes drop out of the sum
+    fpc = 1e9
+    r = bench.step_roofline(N, G, faces, fpc, 1.0, 10.0)
+    t_alu = fpc * N / 1e12 * 1e3
+    assert r["bytes_per_cell"] == per_cell
+    assert r["t_roof_ms"] == pytest.approx((per_cell - clip_bytes) * N * ms_per_byte + t_alu, rel=1e-12)
+    assert r["frac"] == pytest.approx(r["t_roof_ms"] / 10.0)
+    # no flops: every stage bound by its bytes, grid nodes included
+    r = bench.step_roofline(N, 8, faces, 0.0, 1.0, 10.0)
+    assert r["t_roof_ms"] == pytest.approx((per_cell * N + 4 * 8 ** 3) * ms_per_byte, rel=1e-12)
