@@ -154,9 +154,15 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        return self.summarise(self.lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median SM clock, the largest maximum clock and the throttle reasons seen Active, from nvidia-smi's
+        csv lines (fields in the order of Q)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [v.strip() for v in ln.split(",")]
             if len(f) < 9:
                 continue

@@ -52,3 +52,17 @@ def test_step_roofline_takes_the_larger_bound_per_stage():
     # no flops: every stage bound by its bytes, grid nodes included
     r = bench.step_roofline(N, 8, faces, 0.0, 1.0, 10.0)
     assert r["t_roof_ms"] == pytest.approx((per_cell * N + 4 * 8 ** 3) * ms_per_byte, rel=1e-12)
+
+
+def test_clock_samples_summary():
+    lines = ["0, 2070, 2070, 1012.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "0, 1965, 2070, 1398.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, [N/A], 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "garbled line",
+             "0, [N/A], 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    r = bench.Clocks.summarise(lines)
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = ["0, 1500, 2070, 1400, 0x48, Active, Active, Not Active, Not Active"] * 2
+    r = bench.Clocks.summarise(hot)
+    assert r["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and r["sm_mhz"] == 1500.0
+    assert bench.Clocks.summarise([])["sm_mhz"] is None
