@@ -175,6 +175,37 @@ def test_invariance_scale_translate_permute(oracle_mod):
         assert np.array_equal(a, ids4[o4[k]:o4[k + 1]])
 
 
+def test_cell_moments_closed_forms(oracle_mod):
+    """Cell centroid and second moment (integral of |y - x_i|^2) against closed forms: the cubes of the SC
+    lattice (centroid at the site, a^5 / 4), a one-point bounded box (the whole box) and two points split
+    by their bisector (two half boxes)."""
+    n = 8
+    a = 1.0 / n
+    x = inputs.sc_lattice(n)
+    which = np.arange(0, n ** 3, 37)
+    r = oracle_mod.cells(x, 0.0, 1.0, True, which=which, mode="brute")
+    assert np.allclose(r["cen"], x[which], rtol=0, atol=1e-15)
+    assert np.allclose(r["mom2"], a ** 5 / 4, rtol=1e-12, atol=0)
+
+    def box_moments(lo, hi, p):
+        lo, hi, p = map(np.asarray, (lo, hi, p))
+        V = np.prod(hi - lo)
+        c = 0.5 * (lo + hi)
+        return V, c, V * np.sum((hi - lo) ** 2 / 12.0 + (c - p) ** 2)
+
+    lo, hi, p = [1.0, 2.0, 4.0], [3.5, 3.25, 5.0], [2.0, 3.0, 4.5]
+    r = oracle_mod.cells(np.array([p]), lo, hi, False, mode="brute")
+    V, c, m2 = box_moments(lo, hi, p)
+    assert abs(r["vol"][0] - V) < 1e-14 and np.allclose(r["cen"][0], c, atol=1e-14)
+    assert abs(r["mom2"][0] - m2) < 1e-13 * m2
+    pts = np.array([[0.2, 0.3, 0.6], [0.8, 0.3, 0.6]])  # bisector x = 0.5
+    r = oracle_mod.cells(pts, 0.0, 1.0, False, mode="brute")
+    for k, (l0, h0) in enumerate(((0.0, 0.5), (0.5, 1.0))):
+        V, c, m2 = box_moments([l0, 0.0, 0.0], [h0, 1.0, 1.0], pts[k])
+        assert abs(r["vol"][k] - V) < 1e-15 and np.allclose(r["cen"][k], c, atol=1e-15)
+        assert abs(r["mom2"][k] - m2) < 1e-14
+
+
 def test_bounded_box_total_volume(oracle_mod):
     pts, off = inputs.halo_sets(n_sets=3, nmin=64, nmax=400, seed=6, dtype=np.float32)
     for s in range(3):
