@@ -150,6 +150,20 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _arg(t, device, numel, dtype, what):
+    """Host-side check of a tensor handed to the library.  The C ABI takes plain pointers, so a tensor on
+    another device, of another dtype, strided, or too small would be read or written out of bounds; such a
+    tensor raises VT_ERR_INVALID here instead.  None passes (the C call decides whether it is allowed)."""
+    if t is None:
+        return
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.device == device and t.dtype == dtype and t.is_contiguous()
+            and t.numel() >= numel):
+        raise VTError(VT_ERR_INVALID, "%s: needs a contiguous %s tensor on %s with at least %d elements"
+                      % (what, dtype, device, numel))
+
+
 def _stream_ptr(stream):
     import torch
 
@@ -320,29 +334,43 @@ def vt_rebuild(h: Handle, pos, mass=None) -> None:
 def vt_cells(h: Handle, vol=None, nbr_off=None, nbr_id=None, count=True):
     """Fill any of ``vol`` [N], ``nbr_off`` int64 [N+1], ``nbr_id`` int32 [nnz]; returns nnz (None with
     ``count=False``, the form to use inside a CUDA graph capture)."""
+    import torch
+
+    _arg(vol, h.device, h.N, h.dtype, "vt_cells vol")
+    _arg(nbr_off, h.device, h.N + 1, torch.int64, "vt_cells nbr_off")
+    _arg(nbr_id, h.device, 0, torch.int32, "vt_cells nbr_id")
     n = ctypes.c_int64(0)
+    if nbr_id is not None and count:
+        # room for the facets: the size query first (free unless the handle was rebuilt)
+        _check(load_library().vt_cells(h.ptr, None, None, None, ctypes.byref(n)), "vt_cells")
+        _arg(nbr_id, h.device, int(n.value), torch.int32, "vt_cells nbr_id")
     _check(load_library().vt_cells(h.ptr, _ptr(vol), _ptr(nbr_off), _ptr(nbr_id),
                                    ctypes.byref(n) if count else None), "vt_cells")
     return int(n.value) if count else None
 
 
 def vt_density(h: Handle, dens) -> None:
+    _arg(dens, h.device, h.N, h.dtype, "vt_density dens")
     _check(load_library().vt_density(h.ptr, _ptr(dens)), "vt_density")
 
 
 def vt_gradient(h: Handle, grad) -> None:
+    _arg(grad, h.device, 3 * h.N, h.dtype, "vt_gradient grad")
     _check(load_library().vt_gradient(h.ptr, _ptr(grad)), "vt_gradient")
 
 
 def vt_gradient_gg(h: Handle, grad) -> None:
+    _arg(grad, h.device, 3 * h.N, h.dtype, "vt_gradient_gg grad")
     _check(load_library().vt_gradient_gg(h.ptr, _ptr(grad)), "vt_gradient_gg")
 
 
 def vt_grid_density(h: Handle, G: int, S: int, grid) -> None:
+    _arg(grid, h.device, max(int(G), 0) ** 3, h.dtype, "vt_grid_density grid")
     _check(load_library().vt_grid_density(h.ptr, int(G), int(S), _ptr(grid)), "vt_grid_density")
 
 
 def vt_grid_density_volume(h: Handle, G: int, grid) -> None:
+    _arg(grid, h.device, max(int(G), 0) ** 3, h.dtype, "vt_grid_density_volume grid")
     _check(load_library().vt_grid_density_volume(h.ptr, int(G), _ptr(grid)), "vt_grid_density_volume")
 
 
@@ -355,6 +383,8 @@ def grid_density_volume(h: Handle, G: int):
 
 
 def vt_backward_weighted(h: Handle, w, dE_dpos) -> None:
+    _arg(w, h.device, h.N, h.dtype, "vt_backward_weighted w")
+    _arg(dE_dpos, h.device, 3 * h.N, h.dtype, "vt_backward_weighted dE_dpos")
     _check(load_library().vt_backward_weighted(h.ptr, _ptr(w), _ptr(dE_dpos)), "vt_backward_weighted")
 
 
@@ -369,10 +399,14 @@ def backward_weighted(h: Handle, w):
 
 
 def vt_moments(h: Handle, centroid=None, energy=None) -> None:
+    _arg(centroid, h.device, 3 * h.N, h.dtype, "vt_moments centroid")
+    _arg(energy, h.device, h.N, h.dtype, "vt_moments energy")
     _check(load_library().vt_moments(h.ptr, _ptr(centroid), _ptr(energy)), "vt_moments")
 
 
 def vt_backward(h: Handle, dL_dV, dL_dE: float, dL_dpos) -> None:
+    _arg(dL_dV, h.device, h.N, h.dtype, "vt_backward dL_dV")
+    _arg(dL_dpos, h.device, 3 * h.N, h.dtype, "vt_backward dL_dpos")
     _check(load_library().vt_backward(h.ptr, _ptr(dL_dV), float(dL_dE), _ptr(dL_dpos)), "vt_backward")
 
 
@@ -398,6 +432,10 @@ def vt_volumes_noalloc(pos, box_lo, box_hi, periodic, vol, stream=None) -> None:
     (for callers that cannot allocate); ``pos`` and ``vol`` are CUDA tensors the caller owns."""
     import torch
 
+    if not (isinstance(pos, torch.Tensor) and pos.is_cuda and pos.dim() == 2 and pos.shape[1] == 3
+            and pos.dtype in (torch.float32, torch.float64) and pos.is_contiguous()):
+        raise VTError(VT_ERR_INVALID, "vt_volumes_noalloc: pos must be a contiguous CUDA [N,3] float tensor")
+    _arg(vol, pos.device, pos.shape[0], pos.dtype, "vt_volumes_noalloc vol")
     lo = (ctypes.c_double * 3)(*[float(v) for v in (box_lo if hasattr(box_lo, "__len__") else (box_lo,) * 3)])
     hi = (ctypes.c_double * 3)(*[float(v) for v in (box_hi if hasattr(box_hi, "__len__") else (box_hi,) * 3)])
     dt = VT_F32 if pos.dtype == torch.float32 else VT_F64

@@ -157,3 +157,39 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(RuntimeError):
         binding.load_library(str(tmp_path / "missing.so"))
+
+
+def test_binding_checks_tensors_before_the_library_sees_them(lib):
+    """The binding refuses output and input tensors of the wrong dtype, device, layout or size before the C
+    call (which only sees raw pointers).  A handle on the CPU device with no library handle behind it: every
+    call below must be refused by the binding's own check."""
+    import torch
+
+    N = 10
+    h = binding.Handle(None, N, torch.float32, torch.device("cpu"), None)
+    f32 = lambda *s: torch.zeros(*s, dtype=torch.float32)  # noqa: E731
+    bad = {
+        "wrong dtype": torch.zeros(N, dtype=torch.float64),
+        "too small": f32(N - 1),
+        "strided": f32(2 * N)[::2],
+        "not a tensor": [0.0] * N,
+    }
+    for why, t in bad.items():
+        for call in (lambda: binding.vt_cells(h, t), lambda: binding.vt_density(h, t),
+                     lambda: binding.vt_moments(h, None, t), lambda: binding.vt_backward(h, t, 0.0, f32(N, 3)),
+                     lambda: binding.vt_backward_weighted(h, t, f32(N, 3))):
+            with pytest.raises(binding.VTError, match="needs a contiguous") as e:
+                call()
+            assert e.value.code == binding.VT_ERR_INVALID, why
+    for call in (lambda: binding.vt_gradient(h, f32(N, 2)), lambda: binding.vt_gradient_gg(h, f32(N, 2)),
+                 lambda: binding.vt_backward(h, None, 0.0, f32(N, 2)), lambda: binding.vt_moments(h, f32(N, 2)),
+                 lambda: binding.vt_grid_density(h, 4, 1, f32(63)),
+                 lambda: binding.vt_grid_density_volume(h, 4, f32(4, 4, 3)),
+                 lambda: binding.vt_cells(h, None, torch.zeros(N, dtype=torch.int64)),
+                 lambda: binding.vt_cells(h, None, None, torch.zeros(5, dtype=torch.int64))):
+        with pytest.raises(binding.VTError, match="needs a contiguous"):
+            call()
+    # a tensor that passes the check goes on to the library, which refuses the missing handle
+    with pytest.raises(binding.VTError) as e:
+        binding.vt_density(h, f32(N))
+    assert e.value.code == binding.VT_ERR_INVALID and "needs a contiguous" not in str(e.value)
