@@ -193,3 +193,65 @@ def test_binding_checks_tensors_before_the_library_sees_them(lib):
     with pytest.raises(binding.VTError) as e:
         binding.vt_density(h, f32(N))
     assert e.value.code == binding.VT_ERR_INVALID and "needs a contiguous" not in str(e.value)
+
+
+class _FakeLib:
+    """Stands in for libvt_gb300.so: records each call's arguments, answers the size query with `nnz`."""
+
+    def __init__(self, nnz):
+        self.nnz = nnz
+        self.calls = []
+
+    def __getattr__(self, name):
+        def f(*args):
+            self.calls.append((name, args))
+            if name == "vt_cells" and args[4] is not None:
+                args[4]._obj.value = self.nnz
+            return 0
+        return f
+
+
+def test_binding_accepts_the_tensors_its_callers_pass(monkeypatch):
+    """The call patterns of the benchmark step, the captured rebuild step, the per-set loop and the convenience
+    wrappers, against a recording fake of the library on CPU tensors: every valid tensor passes the checks and
+    reaches the C call as its own data pointer."""
+    import torch
+
+    N, G, nnz = 12, 4, 50
+    fake = _FakeLib(nnz)
+    monkeypatch.setattr(binding, "_lib", fake)
+    h = binding.Handle(ctypes.c_void_p(None), N, torch.float32, torch.device("cpu"), None)
+    vol, dens, w = (torch.zeros(N) for _ in range(3))
+    grad, dpos = torch.zeros(N, 3), torch.zeros(N, 3)
+    off = torch.zeros(N + 1, dtype=torch.int64)
+    ids = torch.zeros(24 * N, dtype=torch.int32)
+    grid = torch.zeros(G, G, G)
+    assert binding.vt_cells(h) == nnz
+    assert binding.vt_cells(h, vol, off, ids) == nnz
+    binding.vt_density(h, dens)
+    binding.vt_gradient(h, grad)
+    binding.vt_grid_density(h, G, 1, grid)
+    binding.vt_backward(h, w, 0.0, dpos)
+    binding.vt_moments(h, grad, vol)
+    binding.vt_moments(h, None, vol)
+    assert binding.vt_cells(h, vol, off, None, count=False) is None
+    # per-set slices of whole-batch buffers
+    hs = binding.Handle(ctypes.c_void_p(None), 5, torch.float32, torch.device("cpu"), None)
+    binding.vt_cells(hs, vol[3:8], off[:6], ids[:nnz])
+    binding.vt_density(hs, dens[3:8])
+    binding.vt_gradient(hs, grad[3:8])
+    binding.vt_backward(hs, w[3:8], 0.0, dpos[3:8])
+    # the convenience wrappers allocate on the handle's device
+    v, o, i = binding.cells(h)
+    assert v.shape == (N,) and o.shape == (N + 1,) and i.shape == (nnz,)
+    for r in (binding.density(h), binding.gradient(h), binding.gradient_gg(h), binding.grid_density(h, G),
+              binding.grid_density_volume(h, G), binding.backward(h, torch.ones(N, dtype=torch.float64)),
+              binding.backward_weighted(h, torch.ones(N, dtype=torch.float64)), *binding.moments(h)):
+        assert r.device == h.device and r.dtype == h.dtype
+    names = [c[0] for c in fake.calls]
+    assert "vt_backward_weighted" in names and "vt_grid_density_volume" in names
+    # the pointers are the tensors' own
+    density_calls = [a for n, a in fake.calls if n == "vt_density"]
+    assert density_calls[0][1].value == dens.data_ptr()
+    assert density_calls[1][1].value == dens[3:8].data_ptr()
+    h.ptr = hs.ptr = None
