@@ -499,7 +499,7 @@ def run_ours(args):
                          else None},
             "clocks": clocks,
             "device_counters": {k: stats[-1][k] for k in ("n_cut", "n_tested", "n_passes", "n_fp64_fallbacks",
-                                                          "n_exact_cells", "n_exact_preds", "max_faces",
+                                                          "n_exact_cells", "n_exact_preds", "n_exact_zero", "max_faces",
                                                           "n_handed_over", "n_bucket_passes")}}
     if tuned is not None:
         line["config"]["autotune"] = tuned
