@@ -36,7 +36,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vt_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# VT_ORACLE_SANITIZE=1 builds and loads a separate copy under AddressSanitizer and UndefinedBehaviorSanitizer
+# (the process needs the sanitizer runtimes preloaded: LD_PRELOAD="$(gcc -print-file-name=libasan.so)
+# $(gcc -print-file-name=libubsan.so)" ASAN_OPTIONS=detect_leaks=0).
+_SANITIZE = os.environ.get("VT_ORACLE_SANITIZE") == "1"
+_LIB = os.path.join(_HERE, "liboracle_san.so" if _SANITIZE else "liboracle.so")
 _lib = None
 
 
@@ -44,7 +48,9 @@ def build(force: bool = False) -> str:
     """Compile ``vt_oracle.c`` into ``liboracle.so`` (gcc, OpenMP, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        opt = (["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+                "-fno-sanitize-recover=undefined"] if _SANITIZE else ["-O2"])
+        cmd = ["gcc"] + opt + ["-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB

@@ -657,6 +657,11 @@ static void cand_select(cand_t *c, int64_t n, int64_t k) {
     }
 }
 
+/* candidates in ascending (key, index) order; an empty list (whose buffer may not exist yet) is left alone */
+static void sort_cands(cand_t *c, int64_t n) {
+    if (n > 1) qsort(c, (size_t)n, sizeof(cand_t), cand_cmp);
+}
+
 /* every image (j,s) != (i,0), s in {-1,0,1}^3 (periodic) or s = 0 */
 static int run_brute(cellwork *cw, candbuf *cb) {
     const problem *pb = cw->pb;
@@ -674,7 +679,7 @@ static int run_brute(cellwork *cw, candbuf *cb) {
     /* stage 1: the 64 nearest, in order */
     int64_t k1 = cb->n < 64 ? cb->n : 64;
     cand_select(cb->c, cb->n, k1);
-    qsort(cb->c, k1, sizeof(cand_t), cand_cmp);
+    sort_cands(cb->c, k1);
     int r = clip_sorted(cw, cb->c, k1);
     if (r < 0) return r;
     /* stage 2: every other image whose lower bound does not exclude a cut */
@@ -682,7 +687,7 @@ static int run_brute(cellwork *cw, candbuf *cb) {
     int64_t m = 0;
     for (int64_t k = k1; k < cb->n; k++)
         if (cb->c[k].key <= r2) cb->c[m++] = cb->c[k];
-    qsort(cb->c, m, sizeof(cand_t), cand_cmp);
+    sort_cands(cb->c, m);
     r = clip_sorted(cw, cb->c, m);
     return r < 0 ? r : 0;
 }
@@ -711,7 +716,7 @@ static int run_certified(cellwork *cw, const kdtree *t, candbuf *cb, int64_t lea
                     int s[3] = {sx, sy, sz};
                     kd_query(t, cw->i, s, r_lo2, r_hi2, r + margin, cb);
                 }
-        qsort(cb->c, cb->n, sizeof(cand_t), cand_cmp);
+        sort_cands(cb->c, cb->n);
         int rc = clip_sorted(cw, cb->c, cb->n);
         if (rc < 0) return rc;
         /* every image with key < r^2 has been examined; unexamined ones have
