@@ -62,10 +62,20 @@ def flops_per_cell(w):
     return w["n_cert"] * w["verts"] * 6 + w["verts"] * 40 + w["faces"] * 30
 
 
+def _inputs_tag():
+    """Short hash of the generator module: a cached point set is reused only while its generator is unchanged."""
+    import hashlib
+
+    from paper_1601_06429_gb300 import inputs
+
+    with open(inputs.__file__, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:10]
+
+
 def workload(name):
     from paper_1601_06429_gb300 import inputs
 
-    cache = os.path.join(tempfile.gettempdir(), "vt_bench_%s.npy" % name)
+    cache = os.path.join(tempfile.gettempdir(), "vt_bench_%s_%s.npy" % (name, _inputs_tag()))
     if name == "clustered16M":
         L = 200.0
         gen = lambda: inputs.clustered(16777216, L=L, seed=2)  # noqa: E731

@@ -66,3 +66,18 @@ def test_clock_samples_summary():
     r = bench.Clocks.summarise(hot)
     assert r["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and r["sm_mhz"] == 1500.0
     assert bench.Clocks.summarise([])["sm_mhz"] is None
+
+
+def test_workload_cache_is_keyed_by_the_generator(monkeypatch, tmp_path):
+    # the cached point set is reused only for the same generator source
+    import tempfile
+
+    monkeypatch.setattr(tempfile, "gettempdir", lambda: str(tmp_path))
+    x1, d1 = bench.workload("uniform4096")
+    files = sorted(p.name for p in tmp_path.iterdir())
+    assert files == ["vt_bench_uniform4096_%s.npy" % bench._inputs_tag()]
+    x2, _ = bench.workload("uniform4096")  # from the cache
+    assert (x1 == x2).all() and d1["N"] == 4096 == len(x1)
+    monkeypatch.setattr(bench, "_inputs_tag", lambda: "0123456789")
+    bench.workload("uniform4096")
+    assert len(list(tmp_path.iterdir())) == 2
