@@ -255,3 +255,12 @@ def test_binding_accepts_the_tensors_its_callers_pass(monkeypatch):
     assert density_calls[0][1].value == dens.data_ptr()
     assert density_calls[1][1].value == dens[3:8].data_ptr()
     h.ptr = hs.ptr = None
+
+
+def test_build_lists_every_source_and_header():
+    """Every CUDA translation unit is compiled and every header is a rebuild dependency."""
+    from paper_1601_06429_gb300 import build as b
+
+    files = os.listdir(b.CSRC)
+    assert sorted(f for f in files if f.endswith(".cu")) == sorted(b.SOURCES)
+    assert sorted(f for f in files if f.endswith(".cuh")) == sorted(b.HEADERS)
