@@ -270,6 +270,13 @@ def cpu_oracle_rate_sets(x, off, n_sample, seed=11):
                                              "built inside the timed region), certified mode, FP64" % n_sample)
 
 
+def workload_config(desc, ws):
+    """The workload keys both arms report in ``config``."""
+    G = desc.get("grid", 0)
+    return {"workload": desc["workload"], "grid": "%d^3" % G if G else "none (no single box)",
+            "parallelism": "replicas" if ws > 1 else "1 GPU"}
+
+
 def run_reference(args):
     ws, rank, local = dist_setup(args)
     if rank != 0:
@@ -288,7 +295,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * desc["N"] / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {k: v for k, v in desc.items() if k in ("workload",)},
+            "config": dict(workload_config(desc, ws), precision="fp64 oracle, exact predicates (certified mode)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -482,10 +489,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "filter32" else "f64",
             "data": "synthetic",
-            "config": {"workload": desc["workload"], "precision": args.precision,
-                       "grid": "%d^3" % G if G else "none (no single box)",
-                       "parallelism": "replicas" if ws > 1 else "1 GPU",
-                       "l2": "inputs and workspaces larger than L2 (no flush)"},
+            "config": dict(workload_config(desc, ws), precision=args.precision,
+                           l2="inputs and workspaces larger than L2 (no flush)"),
             "fwd_bwd_breakdown_ms": {"build_sort_tree": sort_ms, "build_clip": clip_ms,
                                      "rest_of_step": ms_step - sort_ms - clip_ms,
                                      "forward": fwd_ms, "grid": grid_ms, "backward": bwd_ms},

@@ -81,3 +81,11 @@ def test_workload_cache_is_keyed_by_the_generator(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "_inputs_tag", lambda: "0123456789")
     bench.workload("uniform4096")
     assert len(list(tmp_path.iterdir())) == 2
+
+
+def test_both_arms_describe_the_same_workload():
+    x, desc = bench.workload("uniform4096")
+    c = bench.workload_config(desc, 1)
+    assert c == {"workload": desc["workload"], "grid": "32^3", "parallelism": "1 GPU"}
+    assert bench.workload_config(dict(desc, grid=0), 2)["grid"].startswith("none")
+    assert bench.workload_config(desc, 2)["parallelism"] == "replicas"
