@@ -217,7 +217,17 @@ def max_over_ranks(v, ws, device=None):
     return float(t.item())
 
 
-HBM_GBS = 6688.8  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+def _hbm_gbs(default=6688.8):
+    """Measured copy bandwidth of the GB300 in GB/s: MEASURED_PEAKS.json's hbm_gbs when the file is present
+    (a STREAM-style copy timed on the same kind of GPU), else the value last measured there."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return default
+
+
+HBM_GBS = _hbm_gbs()
 
 
 def step_roofline(N, G, faces, fpc, peak_tflops, t_ms):
@@ -234,7 +244,7 @@ def step_roofline(N, G, faces, fpc, peak_tflops, t_ms):
     t_alu = fpc * N / (peak_tflops * 1e12) * 1e3
     t_roof = (t_hbm - t_clip_hbm) + max(t_clip_hbm, t_alu)
     return {"t_roof_ms": t_roof, "t_hbm_ms": t_hbm, "t_clip_hbm_ms": t_clip_hbm, "t_clip_alu_ms": t_alu,
-            "t_measured_ms": t_ms, "frac": t_roof / t_ms, "bytes_per_cell": per_cell}
+            "t_measured_ms": t_ms, "frac": t_roof / t_ms, "bytes_per_cell": per_cell, "hbm_gbs": HBM_GBS}
 
 
 def cpu_oracle_rate(x, L, n_sample, seed=11):

@@ -89,3 +89,13 @@ def test_both_arms_describe_the_same_workload():
     assert c == {"workload": desc["workload"], "grid": "32^3", "parallelism": "1 GPU"}
     assert bench.workload_config(dict(desc, grid=0), 2)["grid"].startswith("none")
     assert bench.workload_config(desc, 2)["parallelism"] == "replicas"
+
+
+def test_hbm_peak_comes_from_the_measured_peaks_file(monkeypatch, tmp_path):
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 1234.5}')
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._hbm_gbs() == 1234.5
+    (tmp_path / "MEASURED_PEAKS.json").write_text("not json")
+    assert bench._hbm_gbs(default=7.0) == 7.0
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path / "missing"))
+    assert bench._hbm_gbs(default=8.0) == 8.0
