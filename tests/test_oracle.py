@@ -175,6 +175,32 @@ def test_invariance_scale_translate_permute(oracle_mod):
         assert np.array_equal(a, ids4[o4[k]:o4[k + 1]])
 
 
+def test_rectangular_lattice_in_an_anisotropic_periodic_box(oracle_mod):
+    """A rectangular lattice (spacings 1/4, 2/4, 3/4 in a 1 x 2 x 3 periodic box): every cell is the
+    rectangular box of the spacings, with its six facets at half spacings, and the cells tile the box."""
+    lo, hi = np.zeros(3), np.array([1.0, 2.0, 3.0])
+    n = 4
+    a = hi / n
+    g = [(np.arange(n) + 0.5) * a[c] for c in range(3)]
+    x = np.stack(np.meshgrid(*g, indexing="ij"), -1).reshape(-1, 3)
+    x = x + inputs.rng(3).uniform(-1e-9, 1e-9, x.shape)  # general position
+    r = oracle_mod.cells(x, lo, hi, True, mode="brute")
+    assert abs(r["vol"].sum() - 6.0) < 1e-12
+    assert np.allclose(r["vol"], np.prod(a), rtol=1e-7)
+    off = r["face_off"]
+    big = r["f_area"] > 1e-6 * a.min() ** 2
+    # the six large facets of each cell: areas a_y a_z, a_x a_z, a_x a_y (two each) at half spacings
+    for k in range(0, len(x), 7):
+        sel = np.nonzero(big[off[k]:off[k + 1]])[0] + off[k]
+        assert len(sel) == 6
+        areas = np.sort(r["f_area"][sel])
+        want = np.sort(np.repeat([a[1] * a[2], a[0] * a[2], a[0] * a[1]], 2))
+        assert np.allclose(areas, want, rtol=1e-6)
+        assert np.allclose(np.sort(r["f_dist"][sel]), np.sort(np.repeat(a / 2, 2)), rtol=1e-6)
+    rc = oracle_mod.cells(x, lo, hi, True, mode="certified")
+    assert np.abs(rc["vol"] - r["vol"]).max() < 1e-15
+
+
 def test_cell_moments_closed_forms(oracle_mod):
     """Cell centroid and second moment (integral of |y - x_i|^2) against closed forms: the cubes of the SC
     lattice (centroid at the site, a^5 / 4), a one-point bounded box (the whole box) and two points split
