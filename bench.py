@@ -40,7 +40,7 @@ METRIC = "Voronoi cells/sec (fwd, bwd) at 16.7M clustered pts on 1 GB300; roofli
 UNIT = "cells/s"
 
 # Algorithmic work of one cell, from the oracle on a 2048-cell sample of each workload (seed 7; the table is
-# the output of oracle/work_per_cell.py):
+# the output of tests/work_per_cell.py):
 # W = n_cert * V * 6 + V * 40 + F * 30 flops with n_cert the sites examined before the security stop (every
 # one must be tested against the cell's vertices, 3 FMA each), V the vertices (a vertex from three planes costs
 # about 40 flops) and F the facets of the final cell (about 30 flops each for area, centroid and volume).
@@ -54,8 +54,9 @@ WORK = {
 # DRAM bytes (read + write) of one launch of the clipping kernel, from one ncu capture of this kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/launches_clustered16M.md)
 CLIP_TRAFFIC = {("clustered16M", "filter32"): 10.480e9}
+# FMA lanes per SM of the GB300 (sm_103): 128 FP32; the FP64 rate is 1/64 of it (2 FP64 FMA per clock per SM)
 FP32_LANES_PER_SM = 128
-SM_COUNT = 152
+FP64_LANES_PER_SM = 2
 
 
 def flops_per_cell(w):
@@ -217,14 +218,25 @@ def max_over_ranks(v, ws, device=None):
     return float(t.item())
 
 
+def _measured(key, default):
+    """A field of MEASURED_PEAKS.json (measured on the same kind of GPU), else ``default``."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, ValueError, KeyError, TypeError):
+        return default
+
+
+def alu_peaks(sm_count, sm_max_mhz):
+    """Derived FMA-issue peaks (TFLOP/s) from the unit counts and the maximum SM clock: (FP32, FP64)."""
+    f = sm_count * 2 * sm_max_mhz * 1e6 / 1e12
+    return f * FP32_LANES_PER_SM, f * FP64_LANES_PER_SM
+
+
 def _hbm_gbs(default=6688.8):
     """Measured copy bandwidth of the GB300 in GB/s: MEASURED_PEAKS.json's hbm_gbs when the file is present
     (a STREAM-style copy timed on the same kind of GPU), else the value last measured there."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
-    except (OSError, ValueError, KeyError, TypeError):
-        return default
+    return _measured("hbm_gbs", default)
 
 
 HBM_GBS = _hbm_gbs()
@@ -247,37 +259,43 @@ def step_roofline(N, G, faces, fpc, peak_tflops, t_ms):
             "t_measured_ms": t_ms, "frac": t_roof / t_ms, "bytes_per_cell": per_cell, "hbm_gbs": HBM_GBS}
 
 
-def cpu_oracle_rate(x, L, n_sample, seed=11):
-    """The FP64 oracle (certified mode) on n_sample cells of the same point set; returns (cells/s, info)."""
-    import oracle
+class OracleTimer:
+    """The FP64 oracle (certified mode, all host cores) on random samples of cells of one workload.  The k-d tree
+    over every point is built once, outside the timed region, and its build time is reported beside the rate;
+    each sample is then timed alone, so the rate is cells per second of cell work."""
 
-    oracle.build()
-    which = np.sort(np.random.default_rng(seed).choice(len(x), n_sample, replace=False))
-    x64 = x.astype(np.float64)
-    t0 = time.perf_counter()
-    oracle.cells(x64, 0.0, L, True, which=which, mode="certified")
-    t1 = time.perf_counter()
-    cores = os.cpu_count()
-    return n_sample / (t1 - t0), dict(cores=cores, seconds=t1 - t0,
-                                      sample="%d random cells of the same point set (k-d tree over all %d points "
-                                             "built inside the timed call), certified mode, FP64" % (n_sample, len(x)))
+    def __init__(self, x, desc):
+        import oracle
 
+        oracle.build()
+        self.N = len(x)
+        self.off = desc.get("set_off")
+        t0 = time.perf_counter()
+        if self.off is None:
+            self.trees = [oracle.Tree(x.astype(np.float64), 0.0, desc["L"], True)]
+        else:
+            # bounded sets: one tree per set, each in its box [-1,1]^3
+            self.trees = [oracle.Tree(x[self.off[s]:self.off[s + 1]].astype(np.float64), -1.0, 1.0, False)
+                          for s in range(len(self.off) - 1)]
+        self.tree_seconds = time.perf_counter() - t0
 
-def cpu_oracle_rate_sets(x, off, n_sample, seed=11):
-    """The FP64 oracle (certified mode, bounded boxes [-1,1]^3) on n_sample cells drawn from all sets."""
-    import oracle
-
-    oracle.build()
-    pick = np.sort(np.random.default_rng(seed).choice(len(x), n_sample, replace=False))
-    sid = np.searchsorted(off, pick, side="right") - 1
-    t0 = time.perf_counter()
-    for s in np.unique(sid):
-        xs = x[off[s]:off[s + 1]].astype(np.float64)
-        oracle.cells(xs, -1.0, 1.0, False, which=pick[sid == s] - off[s], mode="certified")
-    t1 = time.perf_counter()
-    return n_sample / (t1 - t0), dict(cores=os.cpu_count(), seconds=t1 - t0,
-                                      sample="%d random cells drawn from all sets (a k-d tree over each touched set "
-                                             "built inside the timed region), certified mode, FP64" % n_sample)
+    def rate(self, n_sample, seed):
+        """(cells/s, info) on n_sample random cells."""
+        pick = np.sort(np.random.default_rng(seed).choice(self.N, n_sample, replace=False))
+        t0 = time.perf_counter()
+        if self.off is None:
+            self.trees[0].cells(pick)
+        else:
+            sid = np.searchsorted(self.off, pick, side="right") - 1
+            for s in np.unique(sid):
+                self.trees[s].cells(pick[sid == s] - self.off[s])
+        dt = time.perf_counter() - t0
+        what = ("%d random cells of the same point set, certified mode, FP64; the k-d tree over all %d points "
+                "(%.1f s, built once outside the timed region) is not in the rate" % (n_sample, self.N,
+                                                                                        self.tree_seconds))
+        if self.off is not None:
+            what = what.replace("the k-d tree over all", "the k-d trees of all sets over")
+        return n_sample / dt, dict(cores=os.cpu_count(), seconds=dt, tree_seconds=self.tree_seconds, sample=what)
 
 
 def workload_config(desc, ws):
@@ -292,22 +310,26 @@ def run_reference(args):
     if rank != 0:
         return 0
     x, desc = workload(args.workload)
+    timer = OracleTimer(x, desc)
     rates = []
     info = None
     for k in range(args.warmup + args.steps):
-        if "set_off" in desc:
-            r, info = cpu_oracle_rate_sets(x, desc["set_off"], args.ref_sample, seed=100 + k)
-        else:
-            r, info = cpu_oracle_rate(x, desc["L"], args.ref_sample, seed=100 + k)
+        r, info = timer.rate(args.cpu_sample, seed=100 + k)
         if k >= args.warmup:
             rates.append(r)
     value = statistics.median(rates)
+    N = desc["N"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * desc["N"] / value,
+            "steps": args.steps, "warmup": args.warmup,
+            # one whole step would be every cell of the workload: extrapolated from the sampled per-cell rate,
+            # plus the one tree build
+            "ms_per_step": 1000.0 * (N / value + timer.tree_seconds),
+            "ms_per_step_kind": "extrapolated: %d cells at the sampled rate + the k-d tree build (%.1f s); each timed "
+                                "step ran %d cells" % (N, timer.tree_seconds, args.cpu_sample),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(desc, ws), precision="fp64 oracle, exact predicates (certified mode)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                             "sample": info["sample"]},
+                             "sample": info["sample"], "tree_seconds": timer.tree_seconds},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -388,8 +410,8 @@ def run_ours(args):
         stats.append(st)
         return nnz
 
-    # measured FP32 FMA throughput (reported beside the derived peak)
-    probe_tflops = vt.vt_probe_fp32_tflops()
+    # measured FMA throughput (reported beside the derived peaks)
+    probe_tflops = vt.vt_probe_fp32_tflops() if args.precision == "filter32" else vt.vt_probe_fp64_tflops()
     # ---------------- device-resident inputs
     for _ in range(args.warmup):
         step(xd)
@@ -490,10 +512,10 @@ def run_ours(args):
     wk = WORK.get(args.workload, WORK["clustered16M"])
     fpc = flops_per_cell(wk)
     achieved = fpc * N / (clip_ms / 1000.0) / 1e12
-    peak_mhz = 2070.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
-    if args.precision == "plain64":
-        peak = peak / 64.0
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_mhz = clocks.get("sm_max_mhz") or _measured("sm_max_mhz", 2070.0)
+    peak32, peak64 = alu_peaks(sm_count, peak_mhz)
+    peak = peak32 if args.precision == "filter32" else peak64
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -516,12 +538,12 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": CLIP_TRAFFIC.get((args.workload, args.precision)),
                          "kernel": "k_clip (clipping, security test, facet emission)",
                          "work": "%.0f algorithmic flops/cell x %d cells per launch" % (fpc, N),
-                         "peak_note": ("FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"
-                                       if args.precision == "filter32" else
-                                       "FP64: 1/64 of the FP32 FMA issue rate, 80.5 / 64 TFLOP/s (derived)"),
-                         "peak_probe": probe_tflops if args.precision == "filter32" else None,
-                         "frac_of_probe": achieved / probe_tflops if probe_tflops > 0 and args.precision == "filter32"
-                         else None},
+                         "peak_note": "%s FMA issue: %d SMs x %d lanes x 2 flop x %.0f MHz (derived)"
+                                      % ("FP32" if args.precision == "filter32" else "FP64", sm_count,
+                                         FP32_LANES_PER_SM if args.precision == "filter32" else FP64_LANES_PER_SM,
+                                         peak_mhz),
+                         "peak_probe": probe_tflops,
+                         "frac_of_probe": achieved / probe_tflops if probe_tflops > 0 else None},
             "clocks": clocks,
             "device_counters": {k: stats[-1][k] for k in ("n_cut", "n_tested", "n_passes", "n_fp64_fallbacks",
                                                           "n_exact_cells", "n_exact_preds", "n_exact_zero", "max_faces",
@@ -531,12 +553,9 @@ def run_ours(args):
     if set_off is not None and not args.no_loop_baseline:
         line["per_set_loop"] = per_set_loop(vt, x, set_off, args.precision, dev, stream, N)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        if set_off is not None:
-            r, info = cpu_oracle_rate_sets(x, set_off, args.cpu_sample)
-        else:
-            r, info = cpu_oracle_rate(x, L, args.cpu_sample)
+        r, info = OracleTimer(x, desc).rate(args.cpu_sample, seed=11)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                                "sample": info["sample"]}
+                                "sample": info["sample"], "tree_seconds": info["tree_seconds"]}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -598,8 +617,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="clustered16M")
     ap.add_argument("--precision", choices=["filter32", "plain64"], default="filter32")
-    ap.add_argument("--cpu-sample", type=int, default=32768)
-    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--cpu-sample", type=int, default=16384,
+                    help="oracle cells per timed sample, in cpu_baseline and in each step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-loop-baseline", action="store_true", help="batched workloads: skip the per-set loop")
     ap.add_argument("--no-autotune", action="store_true", help="batched workloads: default k_target, one warp per cell")

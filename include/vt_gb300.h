@@ -146,10 +146,18 @@ int vt_rebuild(vt_handle h, const void *pos, const void *mass);
  * one FMA = 2 flops): eight independent FMA chains per thread on every SM,
  * best of three timed launches after one untimed (CUDA events).  The
  * denominator of the clipping kernel's ALU roofline (the paper has no
- * counterpart).  Synchronises; allocates 16 KB of device memory for the call.
+ * counterpart).  Synchronises; allocates 32 KB of device memory for the call.
  * Errors: VT_ERR_INVALID (tflops NULL), VT_ERR_OOM, VT_ERR_CUDA.
  */
 int vt_probe_fp32_tflops(double *tflops, void *stream);
+
+/*
+ * vt_probe_fp64_tflops -- measured FP64 FMA throughput of this GPU (TFLOP/s), by the same method as
+ * vt_probe_fp32_tflops on the FP64 pipe (fewer iterations per thread): the denominator of the roofline of the
+ * plain FP64 clipping path.  Synchronises; allocates 32 KB of device memory for the call.  Errors as
+ * vt_probe_fp32_tflops.
+ */
+int vt_probe_fp64_tflops(double *tflops, void *stream);
 
 /* most independent sets one vt_build_batched call takes */
 #define VT_MAX_SETS 65536
@@ -306,9 +314,10 @@ int vt_backward(vt_handle h, const void *dL_dV, double dL_dE, void *dL_dpos);
  * vt_volumes_noalloc -- cell volumes of a small periodic or bounded point set without any device
  * allocation.  The paper has no counterpart: this is for callers that cannot call cudaMalloc (inside
  * another library's memory pool, on hosts that forbid allocation after start-up, or where an allocation
- * would synchronise the device).  It runs the same kernels as vt_build + vt_cells with FP32-filtered
- * clipping, and all of its scratch memory lives in one file-scope device array of about 8 MB that every
- * GPU using the library holds until the process exits.
+ * would synchronise the device).  It runs the same kernels as vt_build + vt_cells with the default
+ * parameters (FP32-filtered clipping, one warp per cell), so the volumes equal theirs bit for bit.  All
+ * of its scratch memory lives in one file-scope device array of about 8 MB that every GPU using the
+ * library holds until the process exits.
  *   pos      device [N][3] (dtype VT_F32 or VT_F64), same rules as vt_build
  *   N        1 <= N <= VT_NOALLOC_MAX_N; larger sets return VT_ERR_CAPACITY
  *   box_lo, box_hi, periodic: as vt_build (periodic boxes need lengths representable in FP32)
@@ -317,7 +326,8 @@ int vt_backward(vt_handle h, const void *dL_dV, double dL_dE, void *dL_dpos);
  * All calls share the array and it keeps the last call's contents; calls whose work overlaps on the GPU
  * (other streams or host threads) race and must be serialised by the caller.  The first call on a device
  * looks up the array's device address with that device current: make that first call before any stream
- * capture.  It calls no cudaMalloc, cudaFree or allocating library routine.  Errors as vt_build, plus
+ * capture; the address is kept, so the entry point must not be used after a cudaDeviceReset of that device.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Errors as vt_build, plus
  * VT_ERR_CAPACITY when the set is too large or its facets do not fit the fixed pool.
  */
 #define VT_NOALLOC_MAX_N 8192
@@ -334,6 +344,15 @@ int vt_status(vt_handle h, vt_stats *out);
  * NULL) an input index whose cell raised it, or -1.  Not part of the paper's method.
  */
 int vt_last_error_detail(int *particle);
+
+/*
+ * vt_debug_fail_alloc -- fault injection for tests (no counterpart in the paper): the nth device allocation
+ * that vt_build or vt_build_batched makes for a handle's workspace from now on (counting from 1) fails as if
+ * cudaMalloc had run out of memory, and the call returns VT_ERR_OOM after freeing what it had allocated.  The
+ * hook fires once and disarms; nth <= 0 disarms it.  Process-wide (all host threads, all devices); returns the
+ * previous setting (0 if the hook was disarmed or has fired).  Touches no device.
+ */
+int vt_debug_fail_alloc(int nth);
 
 /* vt_error_string -- static description of a VT_* code. */
 const char *vt_error_string(int code);

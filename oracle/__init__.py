@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use this package.
 The GPU library never imports it, and it shares no code with the GPU path.
-``work_per_cell.py`` (run by hand, and by a test) prints the oracle's per-cell work counters that
-``bench.py`` keeps as its table of algorithmic flops per cell.
+It imports nothing from the harness either (``tests/work_per_cell.py`` calls it to print the per-cell
+work counters that ``bench.py`` keeps as its table of algorithmic flops per cell).
 
 What each function follows in the paper:
 
@@ -66,6 +66,14 @@ def _load():
         i32 = ctypes.c_int
         lib.oracle_cells.argtypes = [i64, P, P, P, i32, P, i64, i32, i32] + [P] * 16 + [i32]
         lib.oracle_cells.restype = i32
+        lib.oracle_tree_new.argtypes = [i64, P, P, P, i32]
+        lib.oracle_tree_new.restype = P
+        lib.oracle_tree_build_seconds.argtypes = [P]
+        lib.oracle_tree_build_seconds.restype = ctypes.c_double
+        lib.oracle_tree_cells.argtypes = [P, P, i64, i32] + [P] * 16 + [i32]
+        lib.oracle_tree_cells.restype = i32
+        lib.oracle_tree_free.argtypes = [P]
+        lib.oracle_tree_free.restype = None
         lib.oracle_insphere_side.argtypes = [P, P, P, P, P, i32]
         lib.oracle_insphere_side.restype = i32
         lib.oracle_grid_nearest.argtypes = [i64, P, P, P, i32, i32, i32, P, i32]
@@ -107,8 +115,16 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     """
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-    N = pos.shape[0]
     lo, hi = _box(box_lo, box_hi)
+    return _run_cells(pos.shape[0], which, face_cap,
+                      lambda wh, n, out: lib.oracle_cells(pos.shape[0], _ptr(pos), _ptr(lo), _ptr(hi),
+                                                          int(bool(periodic)), _ptr(wh), n,
+                                                          {"brute": 0, "certified": 1}[mode], face_cap, *out,
+                                                          int(nthreads)))
+
+
+def _run_cells(N, which, face_cap, call):
+    """Allocate the per-cell and per-facet outputs, run ``call(which, n, pointers)`` and package the result."""
     if which is None:
         wh = None
         n = N
@@ -131,11 +147,8 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
     f_dist = np.zeros(n * face_cap)
     f_m3 = np.zeros((n * face_cap, 3))
     counters = np.zeros(4, np.int64)
-    rc = lib.oracle_cells(N, _ptr(pos), _ptr(lo), _ptr(hi), int(bool(periodic)), _ptr(wh), n,
-                          {"brute": 0, "certified": 1}[mode], face_cap,
-                          _ptr(vol), _ptr(cen), _ptr(mom2), _ptr(rmax), _ptr(nface), _ptr(nvert), _ptr(nedge),
-                          _ptr(ntest), _ptr(ncut), _ptr(f_nbr), _ptr(f_shift), _ptr(f_area), _ptr(f_cen),
-                          _ptr(f_dist), _ptr(f_m3), _ptr(counters), int(nthreads))
+    rc = call(wh, n, [_ptr(a) for a in (vol, cen, mom2, rmax, nface, nvert, nedge, ntest, ncut, f_nbr, f_shift,
+                                        f_area, f_cen, f_dist, f_m3, counters)])
     if rc != 0:
         raise RuntimeError("oracle_cells failed with code %d on %d cell(s)" % (rc, int(counters[3])))
     nf = nface.astype(np.int64)
@@ -146,6 +159,39 @@ def cells(pos, box_lo=0.0, box_hi=1.0, periodic=True, which=None, mode="brute", 
                 nface=nface, nvert=nvert, nedge=nedge, ntest=ntest, ncut=ncut, face_off=face_off,
                 f_nbr=f_nbr[sel], f_shift=f_shift[sel], f_area=f_area[sel], f_cen=f_cen[sel],
                 f_dist=f_dist[sel], f_m3=f_m3[sel], counters=counters)
+
+
+class Tree:
+    """Certified mode with the k-d tree built once (by the constructor) for many :meth:`cells` calls on the same
+    point set; ``build_seconds`` is the wall time the tree took.  The results equal ``cells(..., mode="certified")``.
+    """
+
+    def __init__(self, pos, box_lo=0.0, box_hi=1.0, periodic=True):
+        self._lib = _load()
+        self.pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        self.lo, self.hi = _box(box_lo, box_hi)
+        self._t = self._lib.oracle_tree_new(self.pos.shape[0], _ptr(self.pos), _ptr(self.lo), _ptr(self.hi),
+                                            int(bool(periodic)))
+        if not self._t:
+            raise MemoryError("oracle_tree_new")
+        self.build_seconds = float(self._lib.oracle_tree_build_seconds(self._t))
+
+    def cells(self, which=None, face_cap=160, nthreads=0):
+        t = self._t
+        return _run_cells(self.pos.shape[0], which, face_cap,
+                          lambda wh, n, out: self._lib.oracle_tree_cells(t, _ptr(wh), n, face_cap, *out,
+                                                                         int(nthreads)))
+
+    def close(self):
+        if self._t:
+            self._lib.oracle_tree_free(self._t)
+            self._t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def neighbours(res, self_ids=None):

@@ -875,25 +875,53 @@ static int extract(cellwork *cw, cellout *co, int face_cap, int64_t *f_nbr, int3
  * counters[0..3] += predicates, exact fallbacks, exact zeros, errors.
  * Returns 0, or the first per-cell error code.
  */
-int oracle_cells(int64_t N, const double *pos, const double *box_lo, const double *box_hi, int periodic,
-                 const int64_t *cells, int64_t n_cells, int mode, int face_cap, double *vol, double *cen,
-                 double *mom2, double *rmax, int32_t *nface, int32_t *nvert, int32_t *nedge, int64_t *ntest,
-                 int64_t *ncut,
-                 int64_t *f_nbr, int32_t *f_shift, double *f_area, double *f_cen, double *f_dist,
-                 double *f_m3, int64_t *counters, int nthreads) {
+/* a problem with its k-d tree (certified mode), kept across calls by oracle_tree_* */
+typedef struct {
     problem pb;
-    pb.N = N; pb.x = pos; pb.periodic = periodic;
-    for (int c = 0; c < 3; c++) { pb.lo[c] = box_lo[c]; pb.hi[c] = box_hi[c]; pb.L[c] = box_hi[c] - box_lo[c]; }
-    if (cells == NULL) n_cells = N;
+    int has_tree;
     kdtree tree;
-    int64_t *leaf_of = NULL;
-    if (mode == 1) {
-        kd_build(&tree, &pb);
-        leaf_of = (int64_t *)malloc(sizeof(int64_t) * (N > 0 ? N : 1));
-        for (int64_t n = 0; n < tree.nn; n++)
-            if (tree.nd[n].left < 0)
-                for (int64_t k = tree.nd[n].a; k < tree.nd[n].b; k++) leaf_of[tree.idx[k]] = n;
+    int64_t *leaf_of;
+    double t_build;  /* seconds spent building the tree */
+} oracle_ctx;
+
+static double wall_seconds(void) {
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    return (double)clock() / CLOCKS_PER_SEC;
+#endif
+}
+
+static void ctx_init(oracle_ctx *cx, int64_t N, const double *pos, const double *box_lo, const double *box_hi,
+                     int periodic, int with_tree) {
+    memset(cx, 0, sizeof(*cx));
+    cx->pb.N = N; cx->pb.x = pos; cx->pb.periodic = periodic;
+    for (int c = 0; c < 3; c++) {
+        cx->pb.lo[c] = box_lo[c]; cx->pb.hi[c] = box_hi[c]; cx->pb.L[c] = box_hi[c] - box_lo[c];
     }
+    if (!with_tree) return;
+    double t0 = wall_seconds();
+    kd_build(&cx->tree, &cx->pb);
+    cx->leaf_of = (int64_t *)malloc(sizeof(int64_t) * (N > 0 ? N : 1));
+    for (int64_t n = 0; n < cx->tree.nn; n++)
+        if (cx->tree.nd[n].left < 0)
+            for (int64_t k = cx->tree.nd[n].a; k < cx->tree.nd[n].b; k++) cx->leaf_of[cx->tree.idx[k]] = n;
+    cx->has_tree = 1;
+    cx->t_build = wall_seconds() - t0;
+}
+
+static void ctx_free(oracle_ctx *cx) {
+    if (cx->has_tree) { kd_free(&cx->tree); free(cx->leaf_of); }
+    cx->has_tree = 0;
+}
+
+/* the cells of the listed particles on a prepared problem: certified mode if it has a tree, else brute force */
+static int ctx_cells(const oracle_ctx *cx, const int64_t *cells, int64_t n_cells, int face_cap, double *vol,
+                     double *cen, double *mom2, double *rmax, int32_t *nface, int32_t *nvert, int32_t *nedge,
+                     int64_t *ntest, int64_t *ncut, int64_t *f_nbr, int32_t *f_shift, double *f_area,
+                     double *f_cen, double *f_dist, double *f_m3, int64_t *counters, int nthreads) {
+    const problem *pbp = &cx->pb;
+    if (cells == NULL) n_cells = pbp->N;
     int64_t tot_pred = 0, tot_exact = 0, tot_zero = 0, tot_err = 0;
     int first_err = 0;
 #ifdef _OPENMP
@@ -902,7 +930,7 @@ int oracle_cells(int64_t N, const double *pos, const double *box_lo, const doubl
 #pragma omp parallel reduction(+ : tot_pred, tot_exact, tot_zero, tot_err)
     {
         cellwork cw;
-        cw.pb = &pb;
+        cw.pb = pbp;
         cw.pl = (plane_t *)malloc(sizeof(plane_t) * MAXP);
         cw.v = (vert_t *)malloc(sizeof(vert_t) * MAXV);
         cw.tmp = (vert_t *)malloc(sizeof(vert_t) * MAXV);
@@ -913,7 +941,7 @@ int oracle_cells(int64_t N, const double *pos, const double *box_lo, const doubl
             int64_t i = cells ? cells[k] : k;
             cw.i = i;
             init_cell(&cw);
-            int rc = (mode == 1) ? run_certified(&cw, &tree, &cb, leaf_of[i]) : run_brute(&cw, &cb);
+            int rc = cx->has_tree ? run_certified(&cw, &cx->tree, &cb, cx->leaf_of[i]) : run_brute(&cw, &cb);
             cellout co;
             memset(&co, 0, sizeof(co));
             if (rc == 0)
@@ -937,9 +965,50 @@ int oracle_cells(int64_t N, const double *pos, const double *box_lo, const doubl
         }
         free(cw.pl); free(cw.v); free(cw.tmp); free(cw.side); free(cb.c);
     }
-    if (mode == 1) { kd_free(&tree); free(leaf_of); }
     counters[0] += tot_pred; counters[1] += tot_exact; counters[2] += tot_zero; counters[3] += tot_err;
     return first_err;
+}
+
+int oracle_cells(int64_t N, const double *pos, const double *box_lo, const double *box_hi, int periodic,
+                 const int64_t *cells, int64_t n_cells, int mode, int face_cap, double *vol, double *cen,
+                 double *mom2, double *rmax, int32_t *nface, int32_t *nvert, int32_t *nedge, int64_t *ntest,
+                 int64_t *ncut,
+                 int64_t *f_nbr, int32_t *f_shift, double *f_area, double *f_cen, double *f_dist,
+                 double *f_m3, int64_t *counters, int nthreads) {
+    oracle_ctx cx;
+    ctx_init(&cx, N, pos, box_lo, box_hi, periodic, mode == 1);
+    int rc = ctx_cells(&cx, cells, n_cells, face_cap, vol, cen, mom2, rmax, nface, nvert, nedge, ntest, ncut,
+                       f_nbr, f_shift, f_area, f_cen, f_dist, f_m3, counters, nthreads);
+    ctx_free(&cx);
+    return rc;
+}
+
+/*
+ * oracle_tree_new / oracle_tree_cells / oracle_tree_free: certified mode with the k-d tree built once and kept,
+ * so that many calls (or a timed call) on the same point set pay for the tree only once.  `pos` must stay valid
+ * until oracle_tree_free.  oracle_tree_build_seconds: the wall time the tree took.  Same outputs as
+ * oracle_cells(mode 1).
+ */
+void *oracle_tree_new(int64_t N, const double *pos, const double *box_lo, const double *box_hi, int periodic) {
+    oracle_ctx *cx = (oracle_ctx *)malloc(sizeof(oracle_ctx));
+    if (cx) ctx_init(cx, N, pos, box_lo, box_hi, periodic, 1);
+    return cx;
+}
+
+double oracle_tree_build_seconds(const void *t) { return ((const oracle_ctx *)t)->t_build; }
+
+int oracle_tree_cells(const void *t, const int64_t *cells, int64_t n_cells, int face_cap, double *vol, double *cen,
+                      double *mom2, double *rmax, int32_t *nface, int32_t *nvert, int32_t *nedge, int64_t *ntest,
+                      int64_t *ncut, int64_t *f_nbr, int32_t *f_shift, double *f_area, double *f_cen,
+                      double *f_dist, double *f_m3, int64_t *counters, int nthreads) {
+    return ctx_cells((const oracle_ctx *)t, cells, n_cells, face_cap, vol, cen, mom2, rmax, nface, nvert, nedge,
+                     ntest, ncut, f_nbr, f_shift, f_area, f_cen, f_dist, f_m3, counters, nthreads);
+}
+
+void oracle_tree_free(void *t) {
+    if (!t) return;
+    ctx_free((oracle_ctx *)t);
+    free(t);
 }
 
 /*

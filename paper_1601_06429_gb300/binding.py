@@ -117,6 +117,10 @@ def load_library(path: str = LIB_PATH):
     lib.vt_volumes_noalloc.restype = i32
     lib.vt_probe_fp32_tflops.argtypes = [ctypes.POINTER(ctypes.c_double), P]
     lib.vt_probe_fp32_tflops.restype = i32
+    lib.vt_probe_fp64_tflops.argtypes = [ctypes.POINTER(ctypes.c_double), P]
+    lib.vt_probe_fp64_tflops.restype = i32
+    lib.vt_debug_fail_alloc.argtypes = [i32]
+    lib.vt_debug_fail_alloc.restype = i32
     lib.vt_last_error_detail.argtypes = [ctypes.POINTER(ctypes.c_int)]
     lib.vt_last_error_detail.restype = i32
     lib.vt_error_string.argtypes = [i32]
@@ -178,11 +182,24 @@ def vt_probe_fp32_tflops(stream=None) -> float:
     return float(v.value)
 
 
+def vt_probe_fp64_tflops(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current GPU in TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(load_library().vt_probe_fp64_tflops(ctypes.byref(v), _stream_ptr(stream)), "vt_probe_fp64_tflops")
+    return float(v.value)
+
+
 def vt_last_error_detail():
     """(reason, particle) of the last failed vt_build on this thread."""
     part = ctypes.c_int(-1)
     det = load_library().vt_last_error_detail(ctypes.byref(part))
     return int(det), int(part.value)
+
+
+def vt_debug_fail_alloc(nth: int) -> int:
+    """Fault injection for tests: the nth workspace allocation of the next builds fails (VT_ERR_OOM);
+    nth <= 0 disarms.  Returns the previous setting."""
+    return int(load_library().vt_debug_fail_alloc(int(nth)))
 
 
 def vt_default_params() -> vt_params:
@@ -436,11 +453,16 @@ def vt_volumes_noalloc(pos, box_lo, box_hi, periodic, vol, stream=None) -> None:
             and pos.dtype in (torch.float32, torch.float64) and pos.is_contiguous()):
         raise VTError(VT_ERR_INVALID, "vt_volumes_noalloc: pos must be a contiguous CUDA [N,3] float tensor")
     _arg(vol, pos.device, pos.shape[0], pos.dtype, "vt_volumes_noalloc vol")
+    if stream is not None and stream.device != pos.device:
+        # the C side launches on the current device and picks that device's scratch array
+        raise VTError(VT_ERR_INVALID, "vt_volumes_noalloc: stream on %s, tensors on %s" % (stream.device, pos.device))
     lo = (ctypes.c_double * 3)(*[float(v) for v in (box_lo if hasattr(box_lo, "__len__") else (box_lo,) * 3)])
     hi = (ctypes.c_double * 3)(*[float(v) for v in (box_hi if hasattr(box_hi, "__len__") else (box_hi,) * 3)])
     dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
-    _check(load_library().vt_volumes_noalloc(_ptr(pos), dt, pos.shape[0], lo, hi, int(bool(periodic)), _ptr(vol),
-                                             _stream_ptr(stream)), "vt_volumes_noalloc")
+    lib = load_library()
+    with torch.cuda.device(pos.device):
+        _check(lib.vt_volumes_noalloc(_ptr(pos), dt, pos.shape[0], lo, hi, int(bool(periodic)), _ptr(vol),
+                                      _stream_ptr(stream)), "vt_volumes_noalloc")
 
 
 # ---------------------------------------------------------------- convenience wrappers

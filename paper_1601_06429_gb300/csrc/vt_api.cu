@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "vt_internal.cuh"
@@ -21,12 +22,28 @@ constexpr unsigned GRID_RETRY_CAP = 1u << 20;  // (cell, voxel) pairs of the vol
 thread_local int g_last_detail = 0;
 thread_local int g_last_particle = -1;
 
+// fault injection (vt_debug_fail_alloc): the number of handle allocations still to succeed before one fails
+// (0: disarmed)
+std::atomic<int> g_fail_alloc{0};
+
+bool injected_failure() {
+    int n = g_fail_alloc.load();
+    while (n > 0) {
+        if (g_fail_alloc.compare_exchange_weak(n, n - 1)) return n == 1;
+    }
+    return false;
+}
+
 struct Alloc {
     bool failed = false;
     template <typename T>
     T* get(size_t count) {
         if (count == 0) count = 1;
         void* p = nullptr;
+        if (injected_failure()) {
+            failed = true;
+            return nullptr;
+        }
         if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
             cudaGetLastError();
             failed = true;
@@ -666,27 +683,34 @@ int vt_status(vt_handle h, vt_stats* out) {
     return d.error ? d.error : VT_OK;
 }
 
-int vt_probe_fp32_tflops(double* tflops, void* stream) {
+}  // extern "C"
+
+namespace {
+// FMA throughput of every SM (TFLOP/s, 2 flops per FMA): best of three timed launches after one untimed
+template <bool F64>
+int probe_fma(double* tflops, void* stream) {
     if (!tflops) return VT_ERR_INVALID;
     *tflops = 0.0;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    float* sink = nullptr;
-    if (cudaMalloc((void**)&sink, 4096 * sizeof(float)) != cudaSuccess) {
+    void* sink = nullptr;
+    if (cudaMalloc(&sink, 4096 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return VT_ERR_OOM;
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int blocks = sms * 8, iters = 4096;
+    // the FP64 pipe is a small fraction of the FP32 one: fewer iterations keep the launch short
+    const int blocks = sms * 8, iters = F64 ? 256 : 4096;
     double best = 0.0;
     int rc = VT_OK;
     for (int rep = 0; rep < 4 && !rc; rep++) {
         cudaEventRecord(e0, s);
-        launch_fma_probe(blocks, iters, sink, s);
+        if (F64) launch_fma_probe64(blocks, iters, (double*)sink, s);
+        else launch_fma_probe(blocks, iters, (float*)sink, s);
         cudaEventRecord(e1, s);
         rc = cuda_rc(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -703,6 +727,15 @@ int vt_probe_fp32_tflops(double* tflops, void* stream) {
     *tflops = best;
     return rc;
 }
+}  // namespace
+
+extern "C" {
+
+int vt_probe_fp32_tflops(double* tflops, void* stream) { return probe_fma<false>(tflops, stream); }
+
+int vt_probe_fp64_tflops(double* tflops, void* stream) { return probe_fma<true>(tflops, stream); }
+
+int vt_debug_fail_alloc(int nth) { return g_fail_alloc.exchange(nth > 0 ? nth : 0); }
 
 int vt_last_error_detail(int* particle) {
     if (particle) *particle = g_last_particle;

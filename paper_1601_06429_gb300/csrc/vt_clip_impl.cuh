@@ -53,7 +53,6 @@ struct Cap {
     static_assert((CAND & (CAND - 1)) == 0, "sort_cand pads the candidates to a power of two up to CAND");
 };
 constexpr int CHUNK = 4;
-constexpr int EXACT_WS = 12288;  // doubles per warp for expansion arithmetic
 
 template <typename CT> struct Prec;
 template <> struct Prec<float> {

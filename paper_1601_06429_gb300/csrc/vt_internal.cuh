@@ -12,6 +12,7 @@ constexpr int STACK_CAP = 192;  // tree traversal stack per warp (fast clipping 
 constexpr int MAX_FACETS = 510; // facets of one cell (the exact kernel's plane capacity minus the initial six)
 constexpr int BUCKET = 32;      // particles per leaf bucket of the search tree
 constexpr int MAX_LEVELS = 8;
+constexpr int EXACT_WS = 12288;  // doubles of expansion-arithmetic workspace per warp of the exact kernel
 
 // cell status bits (per sorted cell)
 constexpr uint8_t CS_DONE = 1;

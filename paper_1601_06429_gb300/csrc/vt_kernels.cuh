@@ -64,6 +64,7 @@ int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaS
 int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
 int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
 int launch_fma_probe(int blocks, int iters, float* sink, cudaStream_t s);
+int launch_fma_probe64(int blocks, int iters, double* sink, cudaStream_t s);
 int launch_cvt_weighted(const void* spos, int dtype, int64_t N, const Geometry& g, const Face* faces,
                         const uint32_t* face_start, const uint16_t* face_count, const CellOut* cell,
                         const uint32_t* perm, const void* w, void* out, int4* retry, unsigned retry_cap,

@@ -13,7 +13,9 @@
 //  * every call shares the array and it keeps the last call's contents; calls
 //    whose work overlaps on the GPU (other streams, other host threads) race;
 //  * the first call on a device looks up the array's device address with that
-//    device current; make that first call before any stream capture.
+//    device current; make that first call before any stream capture.  The address
+//    is kept for the life of the process: a cudaDeviceReset of that device loads
+//    the module again elsewhere, so the entry point must not be used after one.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -41,17 +43,18 @@ constexpr size_t kU8 = align256(kMaxN);
 constexpr size_t kTree = align256(2 * kTreeNodes * 16);
 constexpr size_t kCell = align256(kMaxN * sizeof(vt::CellOut));
 constexpr size_t kFaces = align256((size_t)kMaxN * kFacePool * sizeof(vt::Face));
-constexpr size_t kXws = align256((size_t)kExactWarps * 12288 * 8);
+constexpr size_t kXws = align256((size_t)kExactWarps * vt::EXACT_WS * sizeof(double));
 constexpr size_t kTmp = align256(64 * 1024);
 constexpr size_t kStat = align256(sizeof(vt::DevStatus));
-constexpr size_t kTotal = kSpos + 2 * kKeys + 5 * kU32 + kU16 + kU8 + kTree + kCell + kFaces + kXws + kTmp + kStat;
+constexpr size_t kTotal = kSpos + 2 * kKeys + 4 * kU32 + kU16 + kU8 + kTree + kCell + kFaces + kXws + kTmp + kStat;
 
 __device__ __align__(256) unsigned char g_scratch[kTotal];
 
 std::mutex g_mu;
 unsigned char* g_addr[64] = {nullptr};
 
-// device address of g_scratch on the current device (looked up once per device)
+// device address of g_scratch on the current device (looked up once per device and kept; not valid after a
+// cudaDeviceReset of that device)
 int scratch_address(unsigned char** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
@@ -120,7 +123,6 @@ extern "C" int vt_volumes_noalloc(const void* pos, int dtype, int64_t N, const d
     uint32_t* vals_alt = (uint32_t*)q; q += kU32;
     uint32_t* inv = (uint32_t*)q; q += kU32;
     uint32_t* face_start = (uint32_t*)q; q += kU32;
-    uint32_t* warp_list = (uint32_t*)q; q += kU32;
     uint16_t* face_count = (uint16_t*)q; q += kU16;
     uint8_t* cstat = (uint8_t*)q; q += kU8;
     float4* tree_mem = (float4*)q; q += kTree;
@@ -134,6 +136,7 @@ extern "C" int vt_volumes_noalloc(const void* pos, int dtype, int64_t N, const d
     Tree tree;
     tree_layout(N, tree);
     if (tree.off[0] > kTreeNodes || radix_tmp_bytes(N) > kTmp) return VT_ERR_CAPACITY;
+    if (exact_ws_doubles_per_warp() != (size_t)EXACT_WS) return VT_ERR_CAPACITY;  // the kernel's stride per warp
     tree.lo = tree_mem;
     tree.hi = tree_mem + tree.off[0];
 
@@ -163,7 +166,7 @@ extern "C" int vt_volumes_noalloc(const void* pos, int dtype, int64_t N, const d
     a.st = dstat;
     a.xws = xws;
     a.xws_warps = kExactWarps;
-    a.warp_list = warp_list;
+    a.warp_list = nullptr;  // the warp-per-cell kernel on every cell, as vt_build's default
     launch_clip(a, dtype, VT_FILTER32, sms, s);
     launch_clip_exact(a, dtype, sms, s);
     rc = rc_of(cudaGetLastError());

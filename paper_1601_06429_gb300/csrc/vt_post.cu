@@ -466,23 +466,30 @@ namespace vt {
 // ------------------------------------------------------------------ FP32 FMA throughput probe
 // Eight independent FMA chains per thread, long enough that issue, not latency, bounds the loop; the result is
 // written only if it is impossible (never), so the compiler keeps the work.
-__global__ void __launch_bounds__(256) k_fma_probe(float seed, int iters, float* sink) {
-    float a0 = seed + threadIdx.x, a1 = a0 + 1.f, a2 = a0 + 2.f, a3 = a0 + 3.f, a4 = a0 + 4.f, a5 = a0 + 5.f,
-          a6 = a0 + 6.f, a7 = a0 + 7.f;
-    const float m = 0.999999f, c = 1e-7f;
+// eight independent FMA chains per thread, 16 FMAs each per iteration (FP32 or FP64 pipe)
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T seed, int iters, T* sink) {
+    T a0 = seed + (T)threadIdx.x, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3, a4 = a0 + (T)4, a5 = a0 + (T)5,
+      a6 = a0 + (T)6, a7 = a0 + (T)7;
+    const T m = (T)0.999999, c = (T)1e-7;
     for (int i = 0; i < iters; i++) {
 #pragma unroll
         for (int k = 0; k < 16; k++) {
-            a0 = __fmaf_rn(a0, m, c); a1 = __fmaf_rn(a1, m, c); a2 = __fmaf_rn(a2, m, c); a3 = __fmaf_rn(a3, m, c);
-            a4 = __fmaf_rn(a4, m, c); a5 = __fmaf_rn(a5, m, c); a6 = __fmaf_rn(a6, m, c); a7 = __fmaf_rn(a7, m, c);
+            a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+            a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
         }
     }
-    const float r = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
-    if (r == -1.2345f) sink[blockIdx.x] = r;
+    const T r = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    if (r == (T)-1.2345) sink[blockIdx.x] = r;
 }
 
 int launch_fma_probe(int blocks, int iters, float* sink, cudaStream_t s) {
-    k_fma_probe<<<blocks, 256, 0, s>>>(1.f, iters, sink);
+    k_fma_probe<float><<<blocks, 256, 0, s>>>(1.f, iters, sink);
+    return 1;
+}
+
+int launch_fma_probe64(int blocks, int iters, double* sink, cudaStream_t s) {
+    k_fma_probe<double><<<blocks, 256, 0, s>>>(1.0, iters, sink);
     return 1;
 }
 }  // namespace vt

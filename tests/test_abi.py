@@ -141,6 +141,7 @@ def test_newer_calls_reject_null_arguments(lib):
     assert lib.vt_backward_weighted(None, fake, fake) == binding.VT_ERR_INVALID
     assert lib.vt_moments(None, fake, fake) == binding.VT_ERR_INVALID
     assert lib.vt_probe_fp32_tflops(None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_probe_fp64_tflops(None, None) == binding.VT_ERR_INVALID
 
 
 def test_calls_reject_null_handle(lib):
@@ -264,3 +265,65 @@ def test_build_lists_every_source_and_header():
     files = os.listdir(b.CSRC)
     assert sorted(f for f in files if f.endswith(".cu")) == sorted(b.SOURCES)
     assert sorted(f for f in files if f.endswith(".cuh")) == sorted(b.HEADERS)
+
+
+def test_noalloc_binding_runs_on_the_tensors_device(monkeypatch):
+    """vt_volumes_noalloc launches on the current device and uses that device's scratch array, so the binding
+    makes the tensors' device current around the C call and refuses a stream of another device.  CPU tensors
+    that report a CUDA device stand in for device tensors; a recording fake stands in for the library."""
+    import contextlib
+
+    import torch
+
+    class OnDevice1(torch.Tensor):
+        @property
+        def is_cuda(self):
+            return True
+
+        @property
+        def device(self):
+            return torch.device("cuda", 1)
+
+    class FakeStream:
+        def __init__(self, index):
+            self.device = torch.device("cuda", index)
+            self.cuda_stream = 4242
+
+    current = []
+    seen = []
+
+    @contextlib.contextmanager
+    def fake_device(d):
+        current.append(torch.device(d))
+        try:
+            yield
+        finally:
+            current.pop()
+
+    class Lib:
+        def vt_volumes_noalloc(self, *args):
+            seen.append((current[-1] if current else None, args))
+            return 0
+
+    monkeypatch.setattr(binding, "_lib", Lib())
+    monkeypatch.setattr(torch.cuda, "device", fake_device)
+    monkeypatch.setattr(binding, "_stream_ptr", lambda s: ctypes.c_void_p(s.cuda_stream if s is not None else 7))
+    pos = torch.zeros(16, 3).as_subclass(OnDevice1)
+    vol = torch.zeros(16).as_subclass(OnDevice1)
+    binding.vt_volumes_noalloc(pos, 0.0, 1.0, True, vol)
+    binding.vt_volumes_noalloc(pos, 0.0, 1.0, True, vol, stream=FakeStream(1))
+    assert [d for d, _ in seen] == [torch.device("cuda", 1)] * 2
+    assert seen[1][1][-1].value == 4242 and seen[0][1][0].value == pos.data_ptr()
+    with pytest.raises(binding.VTError) as e:
+        binding.vt_volumes_noalloc(pos, 0.0, 1.0, True, vol, stream=FakeStream(0))
+    assert e.value.code == binding.VT_ERR_INVALID and len(seen) == 2
+
+
+def test_alloc_failure_hook_arms_and_disarms(lib):
+    """The fault-injection hook only sets a host counter: arming returns the previous setting, and nth <= 0
+    disarms it (the GPU tests use it to make a build run out of memory)."""
+    assert lib.vt_debug_fail_alloc(0) == 0
+    assert lib.vt_debug_fail_alloc(3) == 0
+    assert lib.vt_debug_fail_alloc(5) == 3
+    assert lib.vt_debug_fail_alloc(-1) == 5
+    assert lib.vt_debug_fail_alloc(0) == 0

@@ -3,6 +3,7 @@ flop and roofline arithmetic built on it."""
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -13,7 +14,7 @@ import bench  # noqa: E402
 
 def test_work_table_row_matches_the_oracle():
     # the 4096-point row, re-derived from the oracle's counters on the same 2048-cell sample
-    from oracle import work_per_cell
+    import work_per_cell
 
     c = work_per_cell.counters("uniform4096", 2048)
     row = bench.WORK["uniform4096"]
@@ -99,3 +100,24 @@ def test_hbm_peak_comes_from_the_measured_peaks_file(monkeypatch, tmp_path):
     assert bench._hbm_gbs(default=7.0) == 7.0
     monkeypatch.setattr(bench, "ROOT", str(tmp_path / "missing"))
     assert bench._hbm_gbs(default=8.0) == 8.0
+
+
+def test_alu_peaks_from_unit_counts():
+    # 152 SMs at 2070 MHz: 128 FP32 lanes -> 80.5 TFLOP/s; the FP64 pipe is 1/64 of it
+    p32, p64 = bench.alu_peaks(152, 2070.0)
+    assert p32 == pytest.approx(80.54784)
+    assert p64 == pytest.approx(p32 / 64)
+
+
+def test_oracle_timer_rates_cells_without_the_tree():
+    """The CPU baseline's oracle builds its tree once, outside the timed sample, and reports both."""
+    from paper_1601_06429_gb300 import inputs
+
+    x = inputs.uniform(4096, seed=0, dtype=np.float32)
+    t = bench.OracleTimer(x, {"L": 1.0, "N": len(x)})
+    r, info = t.rate(512, seed=1)
+    assert r > 0 and info["tree_seconds"] == t.tree_seconds >= 0 and "512 random cells" in info["sample"]
+    pts, off = inputs.halo_sets(n_sets=3, nmin=100, nmax=400, seed=6)
+    ts = bench.OracleTimer(pts, {"set_off": off, "N": len(pts)})
+    r, info = ts.rate(64, seed=2)
+    assert r > 0 and len(ts.trees) == 3

@@ -153,6 +153,22 @@ def test_brute_equals_certified(poisson, oracle_mod):
     assert np.array_equal(o1, o2) and np.array_equal(n1, n2)
 
 
+def test_kept_tree_equals_certified(poisson, oracle_mod):
+    """The k-d tree built once and kept (oracle.Tree) gives the brute-force cells on any subset, in any order,
+    over several calls; its build time is reported."""
+    x, r = poisson
+    t = oracle_mod.Tree(x, 0.0, 1.0, True)
+    assert t.build_seconds >= 0.0
+    for which in (np.arange(len(x)), np.random.default_rng(3).permutation(len(x))[:300]):
+        c = t.cells(which)
+        assert np.array_equal(c["nface"], r["nface"][which])
+        assert np.abs(c["vol"] - r["vol"][which]).max() < 1e-15
+        o1, n1 = oracle_mod.neighbours(oracle_mod.cells(x, 0.0, 1.0, True, which=which, mode="brute"))
+        o2, n2 = oracle_mod.neighbours(c)
+        assert np.array_equal(o1, o2) and np.array_equal(n1, n2)
+    t.close()
+
+
 def test_invariance_scale_translate_permute(oracle_mod):
     x = inputs.uniform(512, seed=3)
     r = oracle_mod.cells(x, 0.0, 1.0, True, mode="brute")

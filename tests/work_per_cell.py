@@ -1,4 +1,4 @@
-"""Per-cell work counters of the benchmark workloads, from the oracle (test infrastructure).
+"""Per-cell work counters of the benchmark workloads, from the oracle (harness script, run by hand and by a test).
 
 Prints, for each workload of ``bench.py``, the means over a random sample of cells (seed 7) of
   n_cert  planes the oracle examines before the security-radius stop (certified mode: every site
@@ -8,7 +8,7 @@ Prints, for each workload of ``bench.py``, the means over a random sample of cel
 the three numbers of the algorithmic work W = n_cert * verts * 6 + verts * 40 + faces * 30 flops that the
 benchmark divides by the clipping kernel's time.  Nothing here reads the CUDA path.
 
-    python oracle/work_per_cell.py [workload ...] [--sample 2048]
+    python tests/work_per_cell.py [workload ...] [--sample 2048]
 """
 import argparse
 import os
