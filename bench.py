@@ -298,6 +298,44 @@ class OracleTimer:
         return n_sample / dt, dict(cores=os.cpu_count(), seconds=dt, tree_seconds=self.tree_seconds, sample=what)
 
 
+def parity_report(x, L, tree, out, flags, n_sample=2048, n_grad=256, seed=21):
+    """Per-particle errors of one step's outputs against the FP64 oracle (certified mode, on the kept tree) on
+    n_sample random cells plus every cell the exact kernel finished (and up to 256 that needed FP64 decisions):
+    the largest relative volume and density errors, neighbour lists that differ, and for n_grad of the cells
+    (whose neighbours' oracle cells are computed too) the least-squares gradient error
+    |dg| / max(|g_ref|, 1e-3 rho / l), l = V^(1/3), and |dg| / (rho / l) alone.  ``out``: numpy vol, dens, grad,
+    off, ids in input order; ``flags``: vt_cell_flags."""
+    import oracle
+
+    N = len(x)
+    rng = np.random.default_rng(seed)
+    exact = np.nonzero(flags & 2)[0]
+    fp64 = np.nonzero(flags & 1)[0]
+    fp64 = rng.choice(fp64, min(256, len(fp64)), replace=False) if len(fp64) else fp64
+    which = np.unique(np.concatenate([rng.choice(N, n_sample, replace=False), exact, fp64])).astype(np.int64)
+    o = tree.cells(which)
+    vr = np.abs(out["vol"][which] - o["vol"]) / o["vol"]
+    dr = np.abs(out["dens"][which] - 1.0 / o["vol"]) * o["vol"]
+    ooff, oids = oracle.neighbours(o)
+    bad = sum(not np.array_equal(out["ids"][out["off"][i]:out["off"][i + 1]], oids[ooff[k]:ooff[k + 1]])
+              for k, i in enumerate(which))
+    gw = np.sort(rng.choice(which, min(n_grad, len(which)), replace=False))
+    nb = np.unique(np.concatenate([out["ids"][out["off"][i]:out["off"][i + 1]] for i in gw] + [gw]))
+    on = tree.cells(nb)
+    dens_all = np.zeros(N)
+    dens_all[nb] = 1.0 / on["vol"]
+    og = tree.cells(gw)
+    noff, nids, disp = oracle.neighbour_displacements(og, x.astype(np.float64), 0.0, L)
+    g_ref = oracle.gradient(dens_all[gw], noff, nids, disp, dens_all)
+    rho, ell = 1.0 / og["vol"], og["vol"] ** (1.0 / 3.0)
+    dg = np.linalg.norm(out["grad"][gw] - g_ref, axis=1)
+    return {"cells": int(len(which)), "exact_cells": int(len(exact)), "fp64_cells_in_sample": int(len(fp64)),
+            "vol_max_rel": float(vr.max()), "vol_p99_rel": float(np.quantile(vr, 0.99)),
+            "dens_max_rel": float(dr.max()), "nbr_lists_different": int(bad), "grad_cells": int(len(gw)),
+            "grad_max_err_floor_1e-3": float((dg / np.maximum(np.linalg.norm(g_ref, axis=1), 1e-3 * rho / ell)).max()),
+            "grad_max_abs_over_rho_per_l": float((dg / (rho / ell)).max())}
+
+
 def workload_config(desc, ws):
     """The workload keys both arms report in ``config``."""
     G = desc.get("grid", 0)
@@ -553,9 +591,30 @@ def run_ours(args):
     if set_off is not None and not args.no_loop_baseline:
         line["per_set_loop"] = per_set_loop(vt, x, set_off, args.precision, dev, stream, N)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        r, info = OracleTimer(x, desc).rate(args.cpu_sample, seed=11)
+        timer = OracleTimer(x, desc)
+        r, info = timer.rate(args.cpu_sample, seed=11)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                                 "sample": info["sample"], "tree_seconds": info["tree_seconds"]}
+        if set_off is None and not args.no_parity:
+            # per-output error against the oracle: the timed step's outputs, and the other precision's
+            t0 = time.perf_counter()
+            host = lambda t: t.double().cpu().numpy() if t.is_floating_point() else t.cpu().numpy()  # noqa: E731
+            par = {}
+            h = vt.vt_build(xd, None, box[0], box[1], True, args.precision)
+            nnz_last = vt.vt_cells(h)
+            out = dict(vol=host(vol), dens=host(dens), grad=host(grad), off=host(off), ids=host(ids[:nnz_last]))
+            par[args.precision] = parity_report(x, L, timer.trees[0], out, vt.cell_flags(h).cpu().numpy())
+            vt.vt_destroy(h)
+            other = "plain64" if args.precision == "filter32" else "filter32"
+            h = vt.vt_build(xd, None, box[0], box[1], True, other)
+            v2, o2, i2 = vt.cells(h)
+            out = dict(vol=host(v2), dens=host(vt.density(h)), grad=host(vt.gradient(h)), off=host(o2), ids=host(i2))
+            par[other] = parity_report(x, L, timer.trees[0], out, vt.cell_flags(h).cpu().numpy())
+            st2 = vt.vt_status(h)
+            par[other]["clip_ms"] = st2["t_clip_ms"]
+            vt.vt_destroy(h)
+            par["seconds"] = time.perf_counter() - t0
+            line["parity"] = par
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -620,6 +679,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16384,
                     help="oracle cells per timed sample, in cpu_baseline and in each step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true", help="skip the per-output error report against the oracle")
     ap.add_argument("--no-loop-baseline", action="store_true", help="batched workloads: skip the per-set loop")
     ap.add_argument("--no-autotune", action="store_true", help="batched workloads: default k_target, one warp per cell")
     args = ap.parse_args()

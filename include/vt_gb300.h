@@ -226,6 +226,18 @@ int vt_autotune_batched(const void *pos, int dtype, const int64_t *set_off, int 
  */
 int vt_cells(vt_handle h, void *vol, int64_t *nbr_off, int32_t *nbr_id, int64_t *n_faces_out);
 
+/*
+ * vt_cell_flags -- which cells needed the fallbacks of the error-bounded predicates (diagnostics; the paper
+ * has no counterpart, its Qhull runs in one precision).  flags: device uint8 [N], input order, written
+ * asynchronously on the handle's stream: bit 0 (VT_CELL_FP64) some side test of the cell that the FP32
+ * filter could not decide was decided in FP64; bit 1 (VT_CELL_EXACT) the cell was finished by the
+ * exact-predicate kernel (an FP64 test stayed undecided, or the cell outgrew the fast kernel's capacity).
+ * The cells do not depend on the path taken; tests use the flags to make sure such cells are compared.
+ */
+#define VT_CELL_FP64 1
+#define VT_CELL_EXACT 2
+int vt_cell_flags(vt_handle h, uint8_t *flags);
+
 /* vt_density -- density mass/volume (Implementation section).  dens: device [N]. */
 int vt_density(vt_handle h, void *dens);
 

@@ -94,6 +94,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_rebuild.restype = i32
     lib.vt_cells.argtypes = [P, P, P, P, ctypes.POINTER(i64)]
     lib.vt_cells.restype = i32
+    lib.vt_cell_flags.argtypes = [P, P]
+    lib.vt_cell_flags.restype = i32
     lib.vt_density.argtypes = [P, P]
     lib.vt_density.restype = i32
     lib.vt_gradient.argtypes = [P, P]
@@ -364,6 +366,26 @@ def vt_cells(h: Handle, vol=None, nbr_off=None, nbr_id=None, count=True):
     _check(load_library().vt_cells(h.ptr, _ptr(vol), _ptr(nbr_off), _ptr(nbr_id),
                                    ctypes.byref(n) if count else None), "vt_cells")
     return int(n.value) if count else None
+
+
+VT_CELL_FP64 = 1
+VT_CELL_EXACT = 2
+
+
+def vt_cell_flags(h: Handle, flags) -> None:
+    """Fallback flags of every cell into ``flags`` (uint8 [N], input order): VT_CELL_FP64, VT_CELL_EXACT."""
+    import torch
+
+    _arg(flags, h.device, h.N, torch.uint8, "vt_cell_flags flags")
+    _check(load_library().vt_cell_flags(h.ptr, _ptr(flags)), "vt_cell_flags")
+
+
+def cell_flags(h: Handle):
+    import torch
+
+    f = torch.empty(h.N, dtype=torch.uint8, device=h.device)
+    vt_cell_flags(h, f)
+    return f
 
 
 def vt_density(h: Handle, dens) -> None:

@@ -547,6 +547,12 @@ int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t*
     return cuda_rc(cudaGetLastError());
 }
 
+int vt_cell_flags(vt_handle h, uint8_t* flags) {
+    if (!h || !flags) return VT_ERR_INVALID;
+    h->n_launches += launch_cell_flags(h->cstat, h->perm, h->N, flags, h->stream);
+    return cuda_rc(cudaGetLastError());
+}
+
 int vt_density(vt_handle h, void* dens) {
     if (!h || !dens) return VT_ERR_INVALID;
     h->n_launches += launch_density(h->cell, h->spos, h->dtype, h->perm, h->N, h->dens_sorted, dens, h->stream);

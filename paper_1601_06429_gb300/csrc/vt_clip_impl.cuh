@@ -131,6 +131,45 @@ __device__ __forceinline__ void tsum_d(double a, double b, double& s, double& e)
     e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
 }
 
+// Compensated summation (Kahan's method in Neumaier's form): s + c carries the running sum with the rounding
+// error of every addition kept in c, so the result is the exact sum of the terms to within about one rounding
+// of it plus u^2 times the sum of their magnitudes.  FP32 geometry accumulates its facet areas, volumes and
+// moments this way; FP64 geometry sums plainly (its rounding is far below its vertex error).
+template <typename CT>
+struct KSum {
+    CT s, c;
+    __device__ __forceinline__ void zero() { s = (CT)0; c = (CT)0; }
+    __device__ __forceinline__ void add(CT x) { s += x; }
+    __device__ __forceinline__ CT value() const { return s; }
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+};
+template <>
+struct KSum<float> {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void add(float x) {
+        float t, e;
+        tsum_f(s, x, t, e);
+        s = t;
+        c = __fadd_rn(c, e);
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+    // all lanes: the compensated sum over the warp (pairwise, with every level's rounding error kept)
+    __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const float so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
+            float t, e;
+            tsum_f(s, so, t, e);
+            s = t;
+            c = __fadd_rn(__fadd_rn(c, co), e);
+        }
+    }
+};
+
 // one displacement component x_j - x_i (+ shift) with relative error <= u of the working precision.
 // Without a wrap this is one rounded subtraction; with a wrap, x_j - x_i = t + e exactly and t + sL is
 // exact (|t| in [L/2, L]), so one rounding remains.
@@ -1342,7 +1381,8 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
     }
     // facets: lane (chunk c) walks plane c*32+lane; fan from the facet's first vertex
     constexpr int PCH = K::MAXP / 32;
-    CT vol = 0, mzx = 0, mzy = 0, mzz = 0, m2 = 0;
+    KSum<CT> kvol, kzx, kzy, kzz, km2;
+    kvol.zero(); kzx.zero(); kzy.zero(); kzz.zero(); km2.zero();
     CT fA[PCH], fcx[PCH], fcy[PCH], fcz[PCH];
     bool fem[PCH];
 #pragma unroll 1
@@ -1357,7 +1397,8 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         CT x0 = S.tx[t0], y0 = S.ty[t0], z0 = S.tz[t0];
         CT inrm = (CT)1 / S.pnrm[p];
         CT nhx = S.pnx[p] * inrm, nhy = S.pny[p] * inrm, nhz = S.pnz[p] * inrm;
-        CT A_ = 0, csx = 0, csy = 0, csz = 0, sm2 = 0;
+        KSum<CT> kA, kcx, kcy, kcz, ks2;
+        kA.zero(); kcx.zero(); kcy.zero(); kcz.zero(); ks2.zero();
         uint32_t cur = succ_tri<CT, TP>(S, t0, p);
         for (int guard = 0; guard < K::MAXT && cur != t0; guard++) {
             uint32_t nxt = succ_tri<CT, TP>(S, cur, p);
@@ -1369,33 +1410,33 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             CT crx = f_fma<CT>(e1y, e2z, -e1z * e2y), cry = f_fma<CT>(e1z, e2x, -e1x * e2z),
                crz = f_fma<CT>(e1x, e2y, -e1y * e2x);
             CT at = (CT)0.5 * f_fma<CT>(crx, nhx, f_fma<CT>(cry, nhy, crz * nhz));
-            A_ += at;
+            kA.add(at);
             CT third = (CT)(1.0 / 3.0);
-            csx = f_fma<CT>(at * third, x0 + x1 + x2, csx);
-            csy = f_fma<CT>(at * third, y0 + y1 + y2, csy);
-            csz = f_fma<CT>(at * third, z0 + z1 + z2, csz);
+            kcx.add(at * third * (x0 + x1 + x2));
+            kcy.add(at * third * (y0 + y1 + y2));
+            kcz.add(at * third * (z0 + z1 + z2));
             // |y|^2 moment of the tetrahedron (site, v0, v1, v2) without its volume factor
             CT s2 = f_fma<CT>(x0, x0 + x1 + x2, f_fma<CT>(y0, y0 + y1 + y2, z0 * (z0 + z1 + z2)));
             s2 = f_fma<CT>(x1, x1 + x2, f_fma<CT>(y1, y1 + y2, f_fma<CT>(z1, z1 + z2, s2)));
             s2 = f_fma<CT>(x2, x2, f_fma<CT>(y2, y2, f_fma<CT>(z2, z2, s2)));
-            sm2 = f_fma<CT>(at, s2, sm2);
+            ks2.add(at * s2);
             cur = nxt;
         }
+        const CT A_ = kA.value(), csx = kcx.value(), csy = kcy.value(), csz = kcz.value(), sm2 = ks2.value();
         // distance from the site to the facet plane; tetrahedra (site, fan triangle) give
         // V_f = dist A_f / 3, first moment dist * sum(at (v0+v1+v2)/3) / 4, second moment dist/30 * sum(at s2)
         CT dist = S.ph[p] * inrm;
-        vol += dist * A_ * (CT)(1.0 / 3.0);
-        mzx += dist * csx * (CT)0.25;
-        mzy += dist * csy * (CT)0.25;
-        mzz += dist * csz * (CT)0.25;
-        m2 += dist * sm2 * (CT)(1.0 / 30.0);
+        kvol.add(dist * A_ * (CT)(1.0 / 3.0));
+        kzx.add(dist * csx * (CT)0.25);
+        kzy.add(dist * csy * (CT)0.25);
+        kzz.add(dist * csz * (CT)0.25);
+        km2.add(dist * sm2 * (CT)(1.0 / 30.0));
         if (A_ != (CT)0) { fcx[c] = csx / A_; fcy[c] = csy / A_; fcz[c] = csz / A_; }
         fA[c] = A_;
         fem[c] = (p >= 6) && S.pcode[p] < 27;
     }
-    vol = warp_sum<CT>(vol);
-    m2 = warp_sum<CT>(m2);
-    mzx = warp_sum<CT>(mzx); mzy = warp_sum<CT>(mzy); mzz = warp_sum<CT>(mzz);
+    kvol.warp_reduce(); km2.warp_reduce(); kzx.warp_reduce(); kzy.warp_reduce(); kzz.warp_reduce();
+    CT vol = kvol.value(), m2 = km2.value(), mzx = kzx.value(), mzy = kzy.value(), mzz = kzz.value();
     const CT sg = vol < 0 ? (CT)-1 : (CT)1;
     vol *= sg; m2 *= sg;
     int nf_total = 0;
@@ -1470,16 +1511,19 @@ __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
         for (uint32_t q = base; q < base + chunk && q < lim; q++) {
             uint32_t self = EXACT ? A.exact_list[q] : listed ? A.warp_list[q] : q;
             VT_T0(tall);
+            const unsigned f64_before = cc.n_fp64;
             int rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, !EXACT);
             if (rc == RC_RETRY_BOX) rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, false);
             VT_T1(cc, 5, tall);
+            const bool used64 = __any_sync(0xffffffffu, cc.n_fp64 != f64_before);
             __syncwarp();
             if (!EXACT && rc <= -100) rc = RC_NEED_EXACT;  // capacity: the larger exact kernel takes the cell
             if (lane == 0) {
                 if (rc == 0) {
-                    A.cstat[self] = CS_DONE;
+                    A.cstat[self] = EXACT ? (uint8_t)(CS_DONE | CS_EXACT | (A.cstat[self] & CS_FP64))
+                                          : (uint8_t)(CS_DONE | (used64 ? CS_FP64 : 0));
                 } else if (rc == RC_NEED_EXACT) {
-                    A.cstat[self] = CS_NEED_EXACT;
+                    A.cstat[self] = (uint8_t)(CS_NEED_EXACT | (used64 ? CS_FP64 : 0));
                     unsigned slot = atomicAdd(&A.st->n_exact_cells, 1u);
                     A.exact_list[slot] = self;
                 } else {

@@ -512,7 +512,8 @@ __device__ int count_faces(const TCell& C, uint64_t* present) {
 // records go to out[] in plane order.  Returns false if a facet cannot be walked or the volume is not positive.
 __device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& vol, float& mzx, float& mzy,
                            float& mzz, float& m2) {
-    vol = mzx = mzy = mzz = m2 = 0.f;
+    KSum<float> kvol, kzx, kzy, kzz, km2;
+    kvol.zero(); kzx.zero(); kzy.zero(); kzz.zero(); km2.zero();
     int w = 0;
     for (int p = 0; p < C.nP; p++) {
         if (!((present >> p) & 1ull)) continue;
@@ -535,7 +536,8 @@ __device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& v
         const float4 pl = C.Pl[p];
         const float inrm = 1.f / C.Pn[p];
         const float nhx = pl.x * inrm, nhy = pl.y * inrm, nhz = pl.z * inrm;
-        float A_ = 0.f, csx = 0.f, csy = 0.f, csz = 0.f, sm2 = 0.f;
+        KSum<float> kA, kcx, kcy, kcz, ks2;
+        kA.zero(); kcx.zero(); kcy.zero(); kcz.zero(); ks2.zero();
         int cur = -1, steps = 1;
         for (int k = 1; k < m; k++)
             if (fq[k] == fr[0]) { cur = k; break; }
@@ -551,24 +553,25 @@ __device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& v
             const float crx = __fmaf_rn(e1y, e2z, -e1z * e2y), cry = __fmaf_rn(e1z, e2x, -e1x * e2z),
                         crz = __fmaf_rn(e1x, e2y, -e1y * e2x);
             const float at = 0.5f * __fmaf_rn(crx, nhx, __fmaf_rn(cry, nhy, crz * nhz));
-            A_ += at;
+            kA.add(at);
             const float third = (float)(1.0 / 3.0);
-            csx = __fmaf_rn(at * third, v0.x + v1.x + v2.x, csx);
-            csy = __fmaf_rn(at * third, v0.y + v1.y + v2.y, csy);
-            csz = __fmaf_rn(at * third, v0.z + v1.z + v2.z, csz);
+            kcx.add(at * third * (v0.x + v1.x + v2.x));
+            kcy.add(at * third * (v0.y + v1.y + v2.y));
+            kcz.add(at * third * (v0.z + v1.z + v2.z));
             float s2 = __fmaf_rn(v0.x, v0.x + v1.x + v2.x, __fmaf_rn(v0.y, v0.y + v1.y + v2.y, v0.z * (v0.z + v1.z + v2.z)));
             s2 = __fmaf_rn(v1.x, v1.x + v2.x, __fmaf_rn(v1.y, v1.y + v2.y, __fmaf_rn(v1.z, v1.z + v2.z, s2)));
             s2 = __fmaf_rn(v2.x, v2.x, __fmaf_rn(v2.y, v2.y, __fmaf_rn(v2.z, v2.z, s2)));
-            sm2 = __fmaf_rn(at, s2, sm2);
+            ks2.add(at * s2);
             cur = nxt;
         }
         if (steps != m) return false;  // the walk did not close over all of the plane's triangles
+        const float A_ = kA.value(), csx = kcx.value(), csy = kcy.value(), csz = kcz.value(), sm2 = ks2.value();
         const float dist = pl.w * inrm;
-        vol += dist * A_ * (float)(1.0 / 3.0);
-        mzx += dist * csx * 0.25f;
-        mzy += dist * csy * 0.25f;
-        mzz += dist * csz * 0.25f;
-        m2 += dist * sm2 * (float)(1.0 / 30.0);
+        kvol.add(dist * A_ * (float)(1.0 / 3.0));
+        kzx.add(dist * csx * 0.25f);
+        kzy.add(dist * csy * 0.25f);
+        kzz.add(dist * csz * 0.25f);
+        km2.add(dist * sm2 * (float)(1.0 / 30.0));
         if (p >= 6 && C.Pc[p] < 27) {
             Face f;
             f.dx = pl.x; f.dy = pl.y; f.dz = pl.z;
@@ -579,6 +582,7 @@ __device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& v
             out[w++] = f;
         }
     }
+    vol = kvol.value(); mzx = kzx.value(); mzy = kzy.value(); mzz = kzz.value(); m2 = km2.value();
     return vol > 0.f;
 }
 
@@ -689,6 +693,7 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
         // the warp kernel)
         const float Bown = fminf(4.f * rho, 3.f * sqrtf(near2));
         if (alive && mine) fail = init_cell<P>(C, g, pi, self, Bown);
+        const unsigned long long f64_before = tc.fp64;
         bool done = !alive;
         float g2prev = -1.f;
         int streamed = 0;
@@ -809,7 +814,7 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
                 A.cell[self] = co;
                 A.face_start[self] = start;
                 A.face_count[self] = (uint16_t)nf;
-                A.cstat[self] = CS_DONE;
+                A.cstat[self] = (uint8_t)(CS_DONE | (tc.fp64 != f64_before ? CS_FP64 : 0));
                 atomicMax(&A.st->max_faces, (unsigned)nf);
             }
         }

@@ -18,6 +18,8 @@ constexpr int EXACT_WS = 12288;  // doubles of expansion-arithmetic workspace pe
 constexpr uint8_t CS_DONE = 1;
 constexpr uint8_t CS_NEED_EXACT = 2;
 constexpr uint8_t CS_ERROR = 4;
+constexpr uint8_t CS_FP64 = 8;    // FP32 geometry: a side test the FP32 filter left undecided was decided in FP64
+constexpr uint8_t CS_EXACT = 16;  // finished by the exact-predicate kernel
 
 // device-side counters (reset by vt_build, read back at its end)
 struct DevStatus {

@@ -80,6 +80,7 @@ size_t exact_ws_doubles_per_warp();
 
 // post-processing (vt_post.cu)
 int launch_out_vol(const CellOut* cell, const uint32_t* perm, int64_t N, void* vol, int dtype, cudaStream_t s);
+int launch_cell_flags(const uint8_t* cstat, const uint32_t* perm, int64_t N, uint8_t* out, cudaStream_t s);
 int launch_density(const CellOut* cell, const void* spos, int dtype, const uint32_t* perm, int64_t N,
                     double* dens_sorted, void* dens, cudaStream_t s);
 int launch_nbr_count(const uint16_t* face_count, const uint32_t* inv, int64_t N, uint16_t* cnt_in, cudaStream_t s);

@@ -30,6 +30,20 @@ int launch_out_vol(const CellOut* cell, const uint32_t* perm, int64_t N, void* v
     return 1;
 }
 
+// which cells needed a fallback, in input order: bit 0 an FP64 re-decision, bit 1 the exact kernel
+__global__ void k_cell_flags(const uint8_t* __restrict__ cstat, const uint32_t* __restrict__ perm, int64_t N,
+                             uint8_t* __restrict__ out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const uint8_t c = cstat[k];
+    out[perm[k]] = (uint8_t)(((c & CS_FP64) ? 1 : 0) | ((c & CS_EXACT) ? 2 : 0));
+}
+
+int launch_cell_flags(const uint8_t* cstat, const uint32_t* perm, int64_t N, uint8_t* out, cudaStream_t s) {
+    k_cell_flags<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(cstat, perm, N, out);
+    return 1;
+}
+
 // Implementation section: density = particle mass / cell volume
 template <typename P, typename T>
 __global__ void k_density(const CellOut* __restrict__ cell, const P* __restrict__ spos,

@@ -147,6 +147,7 @@ def test_newer_calls_reject_null_arguments(lib):
 def test_calls_reject_null_handle(lib):
     assert lib.vt_cells(None, None, None, None, None) == binding.VT_ERR_INVALID
     assert lib.vt_density(None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_cell_flags(None, None) == binding.VT_ERR_INVALID
     assert lib.vt_gradient(None, None) == binding.VT_ERR_INVALID
     assert lib.vt_grid_density(None, 8, 1, None) == binding.VT_ERR_INVALID
     assert lib.vt_backward(None, None, 0.0, None) == binding.VT_ERR_INVALID

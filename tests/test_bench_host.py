@@ -121,3 +121,27 @@ def test_oracle_timer_rates_cells_without_the_tree():
     ts = bench.OracleTimer(pts, {"set_off": off, "N": len(pts)})
     r, info = ts.rate(64, seed=2)
     assert r > 0 and len(ts.trees) == 3
+
+
+def test_parity_report_of_oracle_outputs_is_exact():
+    """The bench's per-output error report, fed outputs computed by the oracle itself (brute force): zero
+    errors, identical neighbour lists; a perturbed volume shows up as its relative error."""
+    import oracle
+    from paper_1601_06429_gb300 import inputs
+
+    x = inputs.uniform(1024, seed=5)
+    o = oracle.cells(x, 0.0, 1.0, True, mode="brute")
+    off, ids = oracle.neighbours(o)
+    dens = 1.0 / o["vol"]
+    noff, nids, disp = oracle.neighbour_displacements(o, x, 0.0, 1.0)
+    grad = oracle.gradient(dens, noff, nids, disp, dens)
+    out = dict(vol=o["vol"].copy(), dens=dens, grad=grad, off=off, ids=ids)
+    flags = np.zeros(len(x), np.uint8)
+    flags[7] = 2
+    tree = oracle.Tree(x, 0.0, 1.0, True)
+    r = bench.parity_report(x, 1.0, tree, out, flags, n_sample=300, n_grad=40)
+    assert r["nbr_lists_different"] == 0 and r["exact_cells"] == 1
+    assert r["vol_max_rel"] < 1e-14 and r["dens_max_rel"] < 1e-14 and r["grad_max_err_floor_1e-3"] < 1e-9
+    out["vol"][7] *= 1 + 3e-6
+    assert bench.parity_report(x, 1.0, tree, out, flags, n_sample=300, n_grad=40)["vol_max_rel"] == \
+        pytest.approx(3e-6, rel=1e-6)
