@@ -78,6 +78,8 @@ def _load():
         lib.oracle_insphere_side.restype = i32
         lib.oracle_grid_nearest.argtypes = [i64, P, P, P, i32, i32, i32, P, i32]
         lib.oracle_grid_nearest.restype = i32
+        lib.oracle_nearest_points.argtypes = [i64, P, P, P, i32, i64, P, P, i32]
+        lib.oracle_nearest_points.restype = i32
         lib.oracle_grid_point.argtypes = [P, P, i32, i32, i64, i64, P]
         lib.oracle_grid_volume.argtypes = [i64, P, P, P, i32, i32, P, P, P, i32]
         lib.oracle_grid_volume.restype = i32
@@ -318,6 +320,19 @@ def grid_nearest(pos, box_lo, box_hi, G, S=1, periodic=True, nthreads=0):
     out = np.zeros((G ** 3, S ** 3), np.int64)
     lib.oracle_grid_nearest(pos.shape[0], _ptr(pos), _ptr(lo), _ptr(hi), int(bool(periodic)), G, S, _ptr(out),
                             int(nthreads))
+    return out
+
+
+def nearest_points(pos, queries, box_lo, box_hi, periodic=True, nthreads=0):
+    """Index of the nearest particle of each query point (brute force, ties to the lower index, the distance
+    evaluated as in :func:`grid_nearest`).  Returns [M] int64."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    q = np.ascontiguousarray(queries, dtype=np.float64).reshape(-1, 3)
+    lo, hi = _box(box_lo, box_hi)
+    out = np.zeros(q.shape[0], np.int64)
+    lib.oracle_nearest_points(pos.shape[0], _ptr(pos), _ptr(lo), _ptr(hi), int(bool(periodic)), q.shape[0], _ptr(q),
+                              _ptr(out), int(nthreads))
     return out
 
 

@@ -1094,6 +1094,40 @@ int oracle_grid_nearest(int64_t N, const double *pos, const double *box_lo, cons
     return 0;
 }
 
+/*
+ * oracle_nearest_points: for each of M query points q (FP64, [M][3]), the index of the nearest particle under
+ * the periodic (or plain) metric, ties to the lower index, with the squared distance evaluated exactly as in
+ * oracle_grid_nearest.  Brute force over all particles.  out: [M] int64.
+ */
+int oracle_nearest_points(int64_t N, const double *pos, const double *box_lo, const double *box_hi, int periodic,
+                          int64_t M, const double *q, int64_t *out, int nthreads) {
+    double L[3];
+    for (int c = 0; c < 3; c++) L[c] = box_hi[c] - box_lo[c];
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t m = 0; m < M; m++) {
+        double best = INFINITY;
+        int64_t bj = -1;
+        for (int64_t j = 0; j < N; j++) {
+            double d[3];
+            for (int k = 0; k < 3; k++) {
+                double t = pos[3 * j + k] - q[3 * m + k];
+                if (periodic) {
+                    if (t > 0.5 * L[k]) t -= L[k];
+                    else if (t < -0.5 * L[k]) t += L[k];
+                }
+                d[k] = t;
+            }
+            double d2 = fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
+            if (d2 < best) { best = d2; bj = j; }
+        }
+        out[m] = bj;
+    }
+    return 0;
+}
+
 /* FP64 sample point of grid node (a,b,c), sub-point (u,v,w): helper for tests */
 void oracle_grid_point(const double *box_lo, const double *box_hi, int G, int S, int64_t node, int64_t sp,
                        double *g) {

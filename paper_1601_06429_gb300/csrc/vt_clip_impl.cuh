@@ -133,8 +133,8 @@ __device__ __forceinline__ void tsum_d(double a, double b, double& s, double& e)
 
 // Compensated summation (Kahan's method in Neumaier's form): s + c carries the running sum with the rounding
 // error of every addition kept in c, so the result is the exact sum of the terms to within about one rounding
-// of it plus u^2 times the sum of their magnitudes.  FP32 geometry accumulates its facet areas, volumes and
-// moments this way; FP64 geometry sums plainly (its rounding is far below its vertex error).
+// of it plus u^2 times the sum of their magnitudes.  FP32 geometry accumulates its facet areas and cell volumes
+// this way; FP64 geometry sums plainly (its rounding is far below its vertex error).
 template <typename CT>
 struct KSum {
     CT s, c;
@@ -1381,8 +1381,10 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
     }
     // facets: lane (chunk c) walks plane c*32+lane; fan from the facet's first vertex
     constexpr int PCH = K::MAXP / 32;
-    KSum<CT> kvol, kzx, kzy, kzz, km2;
-    kvol.zero(); kzx.zero(); kzy.zero(); kzz.zero(); km2.zero();
+    // the volume (and each facet area) is summed with compensation; the moments plainly
+    KSum<CT> kvol;
+    kvol.zero();
+    CT mzx = 0, mzy = 0, mzz = 0, m2 = 0;
     CT fA[PCH], fcx[PCH], fcy[PCH], fcz[PCH];
     bool fem[PCH];
 #pragma unroll 1
@@ -1397,8 +1399,9 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         CT x0 = S.tx[t0], y0 = S.ty[t0], z0 = S.tz[t0];
         CT inrm = (CT)1 / S.pnrm[p];
         CT nhx = S.pnx[p] * inrm, nhy = S.pny[p] * inrm, nhz = S.pnz[p] * inrm;
-        KSum<CT> kA, kcx, kcy, kcz, ks2;
-        kA.zero(); kcx.zero(); kcy.zero(); kcz.zero(); ks2.zero();
+        KSum<CT> kA;
+        kA.zero();
+        CT csx = 0, csy = 0, csz = 0, sm2 = 0;
         uint32_t cur = succ_tri<CT, TP>(S, t0, p);
         for (int guard = 0; guard < K::MAXT && cur != t0; guard++) {
             uint32_t nxt = succ_tri<CT, TP>(S, cur, p);
@@ -1412,31 +1415,33 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             CT at = (CT)0.5 * f_fma<CT>(crx, nhx, f_fma<CT>(cry, nhy, crz * nhz));
             kA.add(at);
             CT third = (CT)(1.0 / 3.0);
-            kcx.add(at * third * (x0 + x1 + x2));
-            kcy.add(at * third * (y0 + y1 + y2));
-            kcz.add(at * third * (z0 + z1 + z2));
+            csx = f_fma<CT>(at * third, x0 + x1 + x2, csx);
+            csy = f_fma<CT>(at * third, y0 + y1 + y2, csy);
+            csz = f_fma<CT>(at * third, z0 + z1 + z2, csz);
             // |y|^2 moment of the tetrahedron (site, v0, v1, v2) without its volume factor
             CT s2 = f_fma<CT>(x0, x0 + x1 + x2, f_fma<CT>(y0, y0 + y1 + y2, z0 * (z0 + z1 + z2)));
             s2 = f_fma<CT>(x1, x1 + x2, f_fma<CT>(y1, y1 + y2, f_fma<CT>(z1, z1 + z2, s2)));
             s2 = f_fma<CT>(x2, x2, f_fma<CT>(y2, y2, f_fma<CT>(z2, z2, s2)));
-            ks2.add(at * s2);
+            sm2 = f_fma<CT>(at, s2, sm2);
             cur = nxt;
         }
-        const CT A_ = kA.value(), csx = kcx.value(), csy = kcy.value(), csz = kcz.value(), sm2 = ks2.value();
+        const CT A_ = kA.value();
         // distance from the site to the facet plane; tetrahedra (site, fan triangle) give
         // V_f = dist A_f / 3, first moment dist * sum(at (v0+v1+v2)/3) / 4, second moment dist/30 * sum(at s2)
         CT dist = S.ph[p] * inrm;
         kvol.add(dist * A_ * (CT)(1.0 / 3.0));
-        kzx.add(dist * csx * (CT)0.25);
-        kzy.add(dist * csy * (CT)0.25);
-        kzz.add(dist * csz * (CT)0.25);
-        km2.add(dist * sm2 * (CT)(1.0 / 30.0));
+        mzx += dist * csx * (CT)0.25;
+        mzy += dist * csy * (CT)0.25;
+        mzz += dist * csz * (CT)0.25;
+        m2 += dist * sm2 * (CT)(1.0 / 30.0);
         if (A_ != (CT)0) { fcx[c] = csx / A_; fcy[c] = csy / A_; fcz[c] = csz / A_; }
         fA[c] = A_;
         fem[c] = (p >= 6) && S.pcode[p] < 27;
     }
-    kvol.warp_reduce(); km2.warp_reduce(); kzx.warp_reduce(); kzy.warp_reduce(); kzz.warp_reduce();
-    CT vol = kvol.value(), m2 = km2.value(), mzx = kzx.value(), mzy = kzy.value(), mzz = kzz.value();
+    kvol.warp_reduce();
+    CT vol = kvol.value();
+    m2 = warp_sum<CT>(m2);
+    mzx = warp_sum<CT>(mzx); mzy = warp_sum<CT>(mzy); mzz = warp_sum<CT>(mzz);
     const CT sg = vol < 0 ? (CT)-1 : (CT)1;
     vol *= sg; m2 *= sg;
     int nf_total = 0;

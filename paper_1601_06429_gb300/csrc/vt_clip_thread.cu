@@ -512,8 +512,9 @@ __device__ int count_faces(const TCell& C, uint64_t* present) {
 // records go to out[] in plane order.  Returns false if a facet cannot be walked or the volume is not positive.
 __device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& vol, float& mzx, float& mzy,
                            float& mzz, float& m2) {
-    KSum<float> kvol, kzx, kzy, kzz, km2;
-    kvol.zero(); kzx.zero(); kzy.zero(); kzz.zero(); km2.zero();
+    KSum<float> kvol;
+    kvol.zero();
+    mzx = mzy = mzz = m2 = 0.f;
     int w = 0;
     for (int p = 0; p < C.nP; p++) {
         if (!((present >> p) & 1ull)) continue;
@@ -536,8 +537,9 @@ __device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& v
         const float4 pl = C.Pl[p];
         const float inrm = 1.f / C.Pn[p];
         const float nhx = pl.x * inrm, nhy = pl.y * inrm, nhz = pl.z * inrm;
-        KSum<float> kA, kcx, kcy, kcz, ks2;
-        kA.zero(); kcx.zero(); kcy.zero(); kcz.zero(); ks2.zero();
+        KSum<float> kA;
+        kA.zero();
+        float csx = 0.f, csy = 0.f, csz = 0.f, sm2 = 0.f;
         int cur = -1, steps = 1;
         for (int k = 1; k < m; k++)
             if (fq[k] == fr[0]) { cur = k; break; }
@@ -555,23 +557,23 @@ __device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& v
             const float at = 0.5f * __fmaf_rn(crx, nhx, __fmaf_rn(cry, nhy, crz * nhz));
             kA.add(at);
             const float third = (float)(1.0 / 3.0);
-            kcx.add(at * third * (v0.x + v1.x + v2.x));
-            kcy.add(at * third * (v0.y + v1.y + v2.y));
-            kcz.add(at * third * (v0.z + v1.z + v2.z));
+            csx = __fmaf_rn(at * third, v0.x + v1.x + v2.x, csx);
+            csy = __fmaf_rn(at * third, v0.y + v1.y + v2.y, csy);
+            csz = __fmaf_rn(at * third, v0.z + v1.z + v2.z, csz);
             float s2 = __fmaf_rn(v0.x, v0.x + v1.x + v2.x, __fmaf_rn(v0.y, v0.y + v1.y + v2.y, v0.z * (v0.z + v1.z + v2.z)));
             s2 = __fmaf_rn(v1.x, v1.x + v2.x, __fmaf_rn(v1.y, v1.y + v2.y, __fmaf_rn(v1.z, v1.z + v2.z, s2)));
             s2 = __fmaf_rn(v2.x, v2.x, __fmaf_rn(v2.y, v2.y, __fmaf_rn(v2.z, v2.z, s2)));
-            ks2.add(at * s2);
+            sm2 = __fmaf_rn(at, s2, sm2);
             cur = nxt;
         }
         if (steps != m) return false;  // the walk did not close over all of the plane's triangles
-        const float A_ = kA.value(), csx = kcx.value(), csy = kcy.value(), csz = kcz.value(), sm2 = ks2.value();
+        const float A_ = kA.value();
         const float dist = pl.w * inrm;
         kvol.add(dist * A_ * (float)(1.0 / 3.0));
-        kzx.add(dist * csx * 0.25f);
-        kzy.add(dist * csy * 0.25f);
-        kzz.add(dist * csz * 0.25f);
-        km2.add(dist * sm2 * (float)(1.0 / 30.0));
+        mzx += dist * csx * 0.25f;
+        mzy += dist * csy * 0.25f;
+        mzz += dist * csz * 0.25f;
+        m2 += dist * sm2 * (float)(1.0 / 30.0);
         if (p >= 6 && C.Pc[p] < 27) {
             Face f;
             f.dx = pl.x; f.dy = pl.y; f.dz = pl.z;
@@ -582,7 +584,7 @@ __device__ bool emit_faces(const TCell& C, uint64_t present, Face* out, float& v
             out[w++] = f;
         }
     }
-    vol = kvol.value(); mzx = kzx.value(); mzy = kzy.value(); mzz = kzz.value(); m2 = km2.value();
+    vol = kvol.value();
     return vol > 0.f;
 }
 

@@ -1,7 +1,8 @@
 """Differentiation through the Voronoi cells (torch.autograd.Function over vt_backward) and Lloyd steps.
 
-Workload: the 1,048,576-point halo (30 %) + uniform mixture in the unit periodic box, FP32, and a
-32,768-point version of the same recipe for the checks that need the oracle.
+Workload: the 1,048,576-point halo (30 %) + uniform mixture in the unit periodic box, FP32 (the adjoint and
+finite-difference checks on 256 random particles at full size, and the Lloyd steps), and a 32,768-point version
+of the same recipe for the checks over every particle.
 Checks:
   * dL/dx of L = sum_i w_i log(rho_i), w ~ U(0,1), against the oracle's analytic adjoint (all particles)
     and against central finite differences of the oracle's FP64 volumes (h = 1e-4 scaled by the local
@@ -156,3 +157,82 @@ def test_lloyd_runner_matches_autograd_steps_and_graph_replay():
     assert graph.status()["rc"] == 0
     e = np.array(energies)
     assert (np.diff(e) <= 1e-5 * e[:-1]).all()
+
+
+def _local_extract(x64, k, rad):
+    """The points within `rad` (minimum periodic image) of particle k in the unit box, in a frame centred on x_k
+    (no wrap), with their indices; particle k is row 0."""
+    d = x64 - x64[k]
+    d -= np.round(d)
+    sel = np.nonzero((d * d).sum(1) < rad * rad)[0]
+    sel = np.concatenate([[k], sel[sel != k]])
+    return d[sel], sel
+
+
+def test_log_density_adjoint_full_size_config(oracle_mod):
+    """The 1,048,576-point halo (30 %) + uniform set at full size: dL/dx of L = sum_i w_i log(rho_i) (w ~ U(0,1),
+    seed 4) through autograd against the oracle's analytic adjoint on 256 random particles (seed 5), and against
+    central finite differences of the oracle's FP64 volumes with Richardson extrapolation (h_k = 1e-4
+    min(1, l_k / mean l), then h_k / 2).  A cell depends only on the points within twice its largest vertex
+    distance of its site, so each difference is taken on the points near x_k, in a bounded box around them that
+    no cell of interest reaches; the unperturbed extract reproduces the global oracle's volumes first."""
+    N = 1048576
+    x = inputs.halo_uniform_mix(N, L=1.0, seed=3)
+    w = inputs.rng(4).random(N)
+    g, vol = _gpu_grad(x, w, "filter32")
+    h = vt.vt_build(torch.from_numpy(x).cuda(), None, (0.0,) * 3, (1.0,) * 3, True, "filter32")
+    _, noff_g, ids_g = vt.cells(h)
+    noff_g, ids_g = noff_g.cpu().numpy(), ids_g.cpu().numpy()
+    pick = np.sort(np.random.default_rng(5).choice(N, 256, replace=False))
+    x64 = x.astype(np.float64)
+    tree = oracle_mod.Tree(x64, 0.0, 1.0, True)
+    S = np.unique(np.concatenate([pick] + [ids_g[noff_g[k]:noff_g[k + 1]] for k in pick]))
+    o = tree.cells(S)
+    pos_in_S = {int(i): n for n, i in enumerate(S)}
+    ooff, oids = oracle_mod.neighbours(o)
+    for k in pick:
+        n = pos_in_S[int(k)]
+        assert np.array_equal(ids_g[noff_g[k]:noff_g[k + 1]], oids[ooff[n]:ooff[n + 1]]), k
+    # analytic adjoint: every term of dL/dx_k comes from the cells of k and its neighbours, all in S
+    gV = np.zeros(N)
+    gV[S] = -w[S] / o["vol"]
+    ref = oracle_mod.volume_adjoint(o, x64, g_vol=gV)[pick]
+    scale = np.linalg.norm(ref, axis=1)
+    err = np.linalg.norm(g[pick] - ref, axis=1)
+    assert (err <= 1e-4 * scale + 1e-5 * scale.max()).all(), (err / scale).max()
+    # finite differences on local extracts
+    ell = vol ** (1.0 / 3.0)
+    rmax = dict(zip(S.tolist(), o["rmax"]))
+    vS = dict(zip(S.tolist(), o["vol"]))
+    for k in pick:
+        cells_k = np.unique(np.concatenate([[k], ids_g[noff_g[k]:noff_g[k + 1]]]))
+        dist = np.linalg.norm((x64[cells_k] - x64[k]) - np.round(x64[cells_k] - x64[k]), axis=1)
+        reach = max(dist[q] + rmax[int(j)] for q, j in enumerate(cells_k))
+        rad = max(dist[q] + 2.0 * rmax[int(j)] for q, j in enumerate(cells_k)) * 1.05 + 1e-3 * ell[k]
+        loc, sel = _local_extract(x64, k, rad)
+        B = 1.5 * max(rad, reach)
+        order = np.argsort(sel[1:])
+        idx = np.array([0 if j == k else 1 + order[np.searchsorted(sel[1:][order], j)] for j in cells_k])
+        assert (sel[idx] == cells_k).all()
+        r0 = oracle_mod.cells(loc, -B, B, False, which=idx, mode="certified")
+        assert np.allclose(r0["vol"], [vS[int(j)] for j in cells_k], rtol=1e-12, atol=0), k
+        wk = w[cells_k]
+
+        def loss_local(dk):
+            lp = loc.copy()
+            lp[0] += dk
+            return float(np.sum(wk * -np.log(oracle_mod.cells(lp, -B, B, False, which=idx, mode="certified")["vol"])))
+
+        h0 = 1e-4 * min(1.0, ell[k] / ell.mean())
+        for c in range(3):
+            e = np.zeros(3)
+            e[c] = 1.0
+
+            def fd(hh):
+                return (loss_local(hh * e) - loss_local(-hh * e)) / (2 * hh)
+
+            d1, d2 = fd(h0), fd(h0 / 2)
+            rich = (4 * d2 - d1) / 3
+            assert abs(rich - g[k, c]) <= 1e-3 * max(abs(rich), 1e-3 * np.abs(g[k]).max() + 1e-12), (k, c, rich,
+                                                                                                        g[k, c])
+    tree.close()

@@ -191,11 +191,16 @@ def test_batched_errors():
     assert e.value.code == vt.VT_ERR_INVALID
 
 
-def test_halo_sets_4096_sampled(oracle_mod):
+@pytest.fixture(scope="module")
+def sets4096():
+    return inputs.halo_sets()
+
+
+def test_halo_sets_4096_sampled(sets4096, oracle_mod):
     """The 4096-set batch at full size (about 38.7 M points, FP32 filter): every set's volumes sum to its box,
     neighbour lists stay inside their set and are symmetric, and 12 sampled sets (the largest, the smallest and
     10 random ones) match the oracle exactly in their neighbours."""
-    pts, off = inputs.halo_sets()
+    pts, off = sets4096
     n_sets = len(off) - 1
     boxes = unit_boxes(n_sets)
     h, vol, noff, ids = run_batched(pts, off, boxes)
@@ -214,3 +219,48 @@ def test_halo_sets_4096_sampled(oracle_mod):
     pick |= set(inputs.rng(13).choice(n_sets, 10, replace=False).tolist())
     for s in sorted(pick):
         check_set(s, off, boxes[s], vol, noff, ids, pts, oracle_mod, 2e-5)
+
+
+def test_halo_sets_4096_graph_replay(sets4096):
+    """The 4096-set batch as one captured CUDA graph: a batched handle (per-set k_target from the autotuner) is
+    rebuilt inside the capture together with volumes, CSR offsets, densities and gradients; replays on new
+    positions of the same set sizes (each set mirrored through its centre, then the original) equal a fresh
+    batched build of those positions bit for bit, neighbour lists included."""
+    pts, off = sets4096
+    n_sets = len(off) - 1
+    boxes = unit_boxes(n_sets)
+    N = len(pts)
+    set_k, set_tpc = vt.vt_autotune_batched(torch.from_numpy(pts).cuda(), off, boxes, sample=65536)
+    s = torch.cuda.Stream()
+    static = torch.from_numpy(pts).cuda()
+    vol = torch.empty(N, device="cuda")
+    noff = torch.empty(N + 1, dtype=torch.int64, device="cuda")
+    dens = torch.empty(N, device="cuda")
+    grad = torch.empty(N, 3, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        h = vt.vt_build_batched(static, off, boxes, stream=s, set_k=set_k, set_tpc=set_tpc)
+        vt.vt_rebuild(h, static)  # one call outside the capture
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        vt.vt_rebuild(h, static)
+        vt.vt_cells(h, vol, noff, None, count=False)
+        vt.vt_density(h, dens)
+        vt.vt_gradient(h, grad)
+    for new in (-pts, pts):
+        static.copy_(torch.from_numpy(np.ascontiguousarray(new)))
+        g.replay()
+        torch.cuda.synchronize()
+        assert vt.vt_status(h)["rc"] == 0
+        ref = vt.vt_build_batched(torch.from_numpy(np.ascontiguousarray(new)).cuda(), off, boxes, set_k=set_k,
+                                  set_tpc=set_tpc)
+        rv, ro, ri = vt.cells(ref)
+        assert torch.equal(vol, rv) and torch.equal(noff, ro)
+        assert torch.equal(dens, vt.density(ref)) and torch.equal(grad, vt.gradient(ref))
+        n = vt.vt_cells(h)
+        ids = torch.empty(n, dtype=torch.int32, device="cuda")
+        vt.vt_cells(h, None, None, ids)
+        assert torch.equal(ids, ri)
+        vt.vt_destroy(ref)
+    vt.vt_destroy(h)

@@ -479,6 +479,21 @@ def test_grid_nearest_matches_kdtree(oracle_mod):
     assert np.array_equal(idx.reshape(-1), j)
 
 
+def test_nearest_points_matches_grid_nearest_and_kdtree(oracle_mod):
+    """The nearest-particle query for arbitrary points: on the grid's own sub-points it equals grid_nearest, and on
+    random points (periodic and bounded) it equals a scipy k-d tree query."""
+    scipy_spatial = pytest.importorskip("scipy.spatial")
+    x = inputs.uniform(300, seed=4)
+    G, S = 6, 1
+    pts = np.array([oracle_mod.grid_point(0.0, 1.0, G, S, q, 0) for q in range(G ** 3)])
+    assert np.array_equal(oracle_mod.nearest_points(x, pts, 0.0, 1.0, True),
+                          oracle_mod.grid_nearest(x, 0.0, 1.0, G, S, True).reshape(-1))
+    q = np.random.default_rng(2).random((500, 3))
+    assert np.array_equal(oracle_mod.nearest_points(x, q, 0.0, 1.0, True),
+                          scipy_spatial.cKDTree(x, boxsize=1.0).query(q)[1])
+    assert np.array_equal(oracle_mod.nearest_points(x, q, 0.0, 1.0, False), scipy_spatial.cKDTree(x).query(q)[1])
+
+
 def test_grid_density_lattice_constant(oracle_mod):
     x = inputs.sc_lattice(8, perturb=1e-9)
     r = oracle_mod.cells(x, 0.0, 1.0, True, mode="certified")
