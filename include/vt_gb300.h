@@ -123,6 +123,21 @@ int vt_build(vt_handle *h, const void *pos, int dtype, const void *mass, int64_t
              const double box_hi[3], int periodic, const vt_params *p, void *stream);
 
 /*
+ * vt_build_owned -- the cells of the first n_owned particles only, the other N - n_owned being buffer
+ * particles that bound those cells but get none of their own (Implementation section: each task computes
+ * the cells of its sub-volume from its own particles plus the boundary particles of a buffer zone around
+ * it).  Arguments as vt_build, plus
+ *   n_owned  1 <= n_owned <= N: input rows [0, n_owned) are the particles whose cells are computed
+ * The handle answers every call of a vt_build handle; the rows of buffer particles have volume 0, density 0,
+ * no neighbours, a zero gradient and radius 0, while the neighbour lists of computed cells may name them (input
+ * row indices).  A computed cell is the true cell of its particle when every particle within twice its radius
+ * (vt_cell_radius) is in pos; the caller checks that against the extent of its buffer zone (the library
+ * cannot: it sees only the particles it is given).  vt_rebuild keeps n_owned.  Errors as vt_build.
+ */
+int vt_build_owned(vt_handle *h, const void *pos, int dtype, const void *mass, int64_t N, int64_t n_owned,
+                   const double box_lo[3], const double box_hi[3], int periodic, const vt_params *p, void *stream);
+
+/*
  * vt_rebuild -- the cells of new positions for the same particles, in the
  * handle's workspace (the tessellation step again, e.g. for the next Lloyd
  * iteration or the next batch of sets of the same sizes).
@@ -225,6 +240,14 @@ int vt_autotune_batched(const void *pos, int dtype, const int64_t *set_off, int 
  * Inside a stream capture pass nbr_id = NULL and n_faces_out = NULL.
  */
 int vt_cells(vt_handle h, void *vol, int64_t *nbr_off, int32_t *nbr_id, int64_t *n_faces_out);
+
+/*
+ * vt_cell_radius -- the radius of every cell: an upper bound (within about 1e-6 relative) of the largest
+ * distance from the particle to a vertex of its cell (no counterpart in the paper; the security-radius test
+ * stops on it, and a buffer zone must reach twice it).  rad: device [N], input order, dtype of pos;
+ * asynchronous.  Rows whose cell was not computed (vt_build_owned) get 0.
+ */
+int vt_cell_radius(vt_handle h, void *rad);
 
 /*
  * vt_cell_flags -- which cells needed the fallbacks of the error-bounded predicates (diagnostics; the paper

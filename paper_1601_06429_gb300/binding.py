@@ -82,6 +82,11 @@ def load_library(path: str = LIB_PATH):
     lib.vt_build.argtypes = [ctypes.POINTER(P), P, i32, P, i64, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(vt_params), P]
     lib.vt_build.restype = i32
+    lib.vt_build_owned.argtypes = [ctypes.POINTER(P), P, i32, P, i64, i64, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), i32, ctypes.POINTER(vt_params), P]
+    lib.vt_build_owned.restype = i32
+    lib.vt_cell_radius.argtypes = [P, P]
+    lib.vt_cell_radius.restype = i32
     lib.vt_build_batched.argtypes = [ctypes.POINTER(P), P, i32, P, ctypes.POINTER(i64), i32,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(vt_params), P]
@@ -255,6 +260,35 @@ def vt_build(pos, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), per
     return Handle(h, pos.shape[0], pos.dtype, pos.device, stream)
 
 
+def vt_build_owned(pos, n_owned, mass=None, box_lo=(0.0, 0.0, 0.0), box_hi=(1.0, 1.0, 1.0), periodic=True,
+                   precision="filter32", k_target=24, max_passes=1000, face_pool=24, stream=None,
+                   radius_policy=1) -> Handle:
+    """Cells of the first ``n_owned`` rows of ``pos`` (CUDA [N,3]); the other rows are buffer particles."""
+    import torch
+
+    lib = load_library()
+    if not (isinstance(pos, torch.Tensor) and pos.is_cuda and pos.dim() == 2 and pos.shape[1] == 3):
+        raise VTError(VT_ERR_INVALID, "vt_build_owned: pos must be a CUDA [N,3] tensor")
+    if pos.dtype not in (torch.float32, torch.float64):
+        raise VTError(VT_ERR_INVALID, "vt_build_owned: pos dtype")
+    pos = pos.contiguous()
+    if mass is not None:
+        mass = mass.to(device=pos.device, dtype=pos.dtype).contiguous()
+    p = _params(precision, k_target, max_passes, face_pool, radius_policy, 0)
+    lo = (ctypes.c_double * 3)(*[float(v) for v in (box_lo if hasattr(box_lo, "__len__") else (box_lo,) * 3)])
+    hi = (ctypes.c_double * 3)(*[float(v) for v in (box_hi if hasattr(box_hi, "__len__") else (box_hi,) * 3)])
+    h = ctypes.c_void_p()
+    dt = VT_F32 if pos.dtype == torch.float32 else VT_F64
+    with torch.cuda.device(pos.device):
+        rc = lib.vt_build_owned(ctypes.byref(h), _ptr(pos), dt, _ptr(mass), pos.shape[0], int(n_owned), lo, hi,
+                                int(bool(periodic)), ctypes.byref(p), _stream_ptr(stream))
+    if rc != VT_OK:
+        part = ctypes.c_int(-1)
+        det = lib.vt_last_error_detail(ctypes.byref(part))
+        raise VTError(rc, "vt_build_owned", det, part.value)
+    return Handle(h, pos.shape[0], pos.dtype, pos.device, stream)
+
+
 def _params(precision, k_target, max_passes, face_pool, radius_policy, threads_per_cell=0) -> vt_params:
     p = vt_default_params()
     p.precision = {"filter32": VT_FILTER32, "plain64": VT_PLAIN64}[precision] if isinstance(precision, str) \
@@ -366,6 +400,20 @@ def vt_cells(h: Handle, vol=None, nbr_off=None, nbr_id=None, count=True):
     _check(load_library().vt_cells(h.ptr, _ptr(vol), _ptr(nbr_off), _ptr(nbr_id),
                                    ctypes.byref(n) if count else None), "vt_cells")
     return int(n.value) if count else None
+
+
+def vt_cell_radius(h: Handle, rad) -> None:
+    """Bound of each cell's largest vertex distance into ``rad`` ([N], input order, the handle's dtype)."""
+    _arg(rad, h.device, h.N, h.dtype, "vt_cell_radius rad")
+    _check(load_library().vt_cell_radius(h.ptr, _ptr(rad)), "vt_cell_radius")
+
+
+def cell_radius(h: Handle):
+    import torch
+
+    r = torch.empty(h.N, dtype=h.dtype, device=h.device)
+    vt_cell_radius(h, r)
+    return r
 
 
 VT_CELL_FP64 = 1

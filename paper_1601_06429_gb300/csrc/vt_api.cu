@@ -57,7 +57,7 @@ void free_handle(vt_handle h) {
     if (!h) return;
     for (int k = 0; k < 4; k++)
         if (h->ev[k]) cudaEventDestroy(h->ev[k]);
-    void* ptrs[] = {h->spos, h->perm, h->inv, h->tree_mem, h->cell, h->face_start, h->face_count, h->cstat,
+    void* ptrs[] = {h->spos, h->perm, h->inv, h->tree_mem, h->cell, h->face_start, h->face_count, h->cstat, h->rad,
                     h->exact_list, h->dens_sorted, h->faces, h->xws, h->tmp, h->nbr_off_cache, h->dstat,
                     h->keys, h->keys_alt, h->vals_alt, h->cnt_in, h->sset, h->sgeo, h->soff, h->set_in, h->warp_list,
                     h->set_cfg, h->gacc, h->gretry, h->gcnt};
@@ -95,9 +95,23 @@ ClipArgs clip_args(vt_handle h) {
     a.sgeo = h->sgeo;
     a.soff = h->soff;
     const bool thread_first = h->set_cfg ? h->any_thread != 0 : h->prm.threads_per_cell == 1;
-    a.warp_list = thread_first ? h->warp_list : nullptr;
+    a.list_given = h->n_owned < h->N;
+    a.warp_list = (thread_first || a.list_given) ? h->warp_list : nullptr;
     a.set_cfg = h->set_cfg;
+    a.rad = h->rad;
     return a;
+}
+
+// a build over owned and ghost particles: the cells of the ghosts are not computed (volume 0, no facets), and
+// the clipping kernel takes its cells from the list of the owned ones
+int enqueue_owned(vt_handle h) {
+    if (h->n_owned >= h->N) return VT_OK;
+    cudaStream_t s = h->stream;
+    int rc = cuda_rc(cudaMemsetAsync(h->cell, 0, (size_t)h->N * sizeof(CellOut), s));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(h->face_count, 0, (size_t)h->N * sizeof(uint16_t), s));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(h->rad, 0, (size_t)h->N * sizeof(float), s));
+    if (!rc) h->n_launches += launch_owned_list(h->inv, h->n_owned, h->warp_list, h->dstat, s);
+    return rc;
 }
 
 int run_clip(vt_handle h) {
@@ -111,6 +125,8 @@ int run_clip(vt_handle h) {
         int rc = cuda_rc(cudaMemcpyAsync(h->dstat, &z, sizeof(z), cudaMemcpyHostToDevice, s));
         if (rc) return rc;
         rc = cuda_rc(cudaStreamSynchronize(s));
+        if (rc) return rc;
+        rc = enqueue_owned(h);
         if (rc) return rc;
         ClipArgs a = clip_args(h);
         cudaEventRecord(h->ev[2], s);
@@ -230,11 +246,12 @@ void enqueue_sort_tree(vt_handle h, const void* pos, const void* mass) {
 // tables set_off [n_sets+1] and sgeo [n_sets]).
 int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int64_t N, const Geometry& geo,
                int n_sets, const int64_t* set_off, const Geometry* sgeo_host, const int32_t* cfg_host,
-               const vt_params& prm, void* stream) {
+               const vt_params& prm, void* stream, int64_t n_owned = -1) {
     vt_handle h = new (std::nothrow) vt_handle_s;
     if (!h) return VT_ERR_OOM;
     memset(h, 0, sizeof(*h));
     h->N = N;
+    h->n_owned = n_owned >= 0 && n_owned < N ? n_owned : N;
     h->dtype = dtype;
     h->precision = prm.precision;
     h->prm = prm;
@@ -265,6 +282,7 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
     h->cstat = A.get<uint8_t>(N);
     h->exact_list = A.get<uint32_t>(N);
     h->warp_list = A.get<uint32_t>(N);
+    h->rad = A.get<float>(N);
     h->dens_sorted = A.get<double>(N);
     h->face_cap = (uint64_t)N * prm.face_pool;
     h->faces = A.get<Face>(h->face_cap);
@@ -356,6 +374,22 @@ int vt_build(vt_handle* out, const void* pos, int dtype, const void* mass, int64
     rc = make_geometry(box_lo, box_hi, periodic, prm.precision, geo);
     if (rc) return rc;
     return build_impl(out, pos, dtype, mass, N, geo, 0, nullptr, nullptr, nullptr, prm, stream);
+}
+
+int vt_build_owned(vt_handle* out, const void* pos, int dtype, const void* mass, int64_t N, int64_t n_owned,
+                   const double box_lo[3], const double box_hi[3], int periodic, const vt_params* p, void* stream) {
+    if (!out) return VT_ERR_INVALID;
+    *out = nullptr;
+    if (!pos || !box_lo || !box_hi || N < 1 || N > 0x7FFFFFFF / 2 || n_owned < 1 || n_owned > N) return VT_ERR_INVALID;
+    if (dtype != VT_F32 && dtype != VT_F64) return VT_ERR_INVALID;
+    vt_params prm;
+    int rc = check_params(p, prm);
+    if (rc) return rc;
+    if (prm.threads_per_cell == 1) prm.threads_per_cell = 32;  // the listed cells go to the warp kernel
+    Geometry geo;
+    rc = make_geometry(box_lo, box_hi, periodic, prm.precision, geo);
+    if (rc) return rc;
+    return build_impl(out, pos, dtype, mass, N, geo, 0, nullptr, nullptr, nullptr, prm, stream, n_owned);
 }
 
 int vt_build_batched(vt_handle* out, const void* pos, int dtype, const void* mass, const int64_t* set_off, int n_sets,
@@ -505,6 +539,8 @@ int vt_rebuild(vt_handle h, const void* pos, const void* mass) {
     int rc = cuda_rc(cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), s));
     if (rc) return rc;
     enqueue_sort_tree(h, pos, mass);
+    rc = enqueue_owned(h);
+    if (rc) return rc;
     ClipArgs a = clip_args(h);
     h->n_launches += launch_clip(a, h->dtype, h->precision, h->sm_count, s);
     h->n_launches += launch_clip_exact(a, h->dtype, h->sm_count, s);
@@ -544,6 +580,12 @@ int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t*
         if (nbr_id)
             h->n_launches += launch_nbr_emit(h->faces, h->face_start, h->face_count, h->perm, h->inv, off, h->N, nbr_id, s);
     }
+    return cuda_rc(cudaGetLastError());
+}
+
+int vt_cell_radius(vt_handle h, void* rad) {
+    if (!h || !rad) return VT_ERR_INVALID;
+    h->n_launches += launch_out_rad(h->rad, h->perm, h->N, rad, h->dtype, h->stream);
     return cuda_rc(cudaGetLastError());
 }
 
@@ -673,7 +715,7 @@ int vt_status(vt_handle h, vt_stats* out) {
     out->reserved[0] = d.error_detail;
     out->reserved[1] = (int64_t)d.n_collect;
     out->reserved[2] = (int64_t)d.n_collected;
-    out->n_handed_over = (int64_t)d.n_warp_cells;
+    out->n_handed_over = h->n_owned < h->N ? 0 : (int64_t)d.n_warp_cells;
     if (h->gcnt) {
         unsigned gc[2] = {0u, 0u};
         if (cudaMemcpy(gc, h->gcnt, sizeof(gc), cudaMemcpyDeviceToHost) == cudaSuccess) out->n_grid_failed = gc[1];

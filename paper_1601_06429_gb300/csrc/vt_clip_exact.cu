@@ -9,12 +9,18 @@ void launch_clip_f64(const ClipArgs& a, int precision, int sm_count, cudaStream_
 size_t exact_ws_doubles_per_warp() { return EXACT_WS; }
 
 // FP32 filter with a warp list: the thread-per-cell kernel, then the warp kernel on the cells it handed over.
-// Otherwise (plain FP64, or no list) the warp kernel on every cell.
+// A given list (cells of owned particles only): the warp kernel on the listed cells.  Otherwise (plain FP64, or no
+// list) the warp kernel on every cell.
 int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s) {
     int n = 0;
     ClipArgs b = a;
-    if (precision == VT_FILTER32 && a.warp_list) n += launch_clip_thread(a, dtype, sm_count, s);
-    else b.warp_list = nullptr;
+    if (a.list_given) {
+        // the cells to compute are listed: the warp kernel takes exactly those
+    } else if (precision == VT_FILTER32 && a.warp_list) {
+        n += launch_clip_thread(a, dtype, sm_count, s);
+    } else {
+        b.warp_list = nullptr;
+    }
     if (dtype == VT_F32) launch_clip_f32(b, precision, sm_count, s);
     else launch_clip_f64(b, precision, sm_count, s);
     return n + 1;

@@ -671,11 +671,41 @@ __device__ int resolve(const WarpSmem<CT, TP>& S, int s, bool need, uint32_t src
     return sd;
 }
 
+// position of the k-th (from 0) set bit of m; m must have more than k set bits
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w; w >>= 1) {
+        const unsigned lo = m & ((1u << w) - 1u);
+        const int c = __popc(lo);
+        if (k >= c) { k -= c; m >>= w; pos += w; }
+        else m = lo;
+    }
+    return pos;
+}
+// the k lowest set bits of m (all of them if it has k or fewer)
+__device__ __forceinline__ unsigned lowest_set_bits(unsigned m, int k) {
+    if (k <= 0) return 0u;
+    if (k >= __popc(m)) return m;
+    return m & ((1u << nth_set_bit(m, k)) - 1u);
+}
+// element e of a small per-chunk mask array without dynamic register indexing
+template <int TP>
+__device__ __forceinline__ unsigned pick(const unsigned* a, int e) {
+    unsigned r = a[0];
+#pragma unroll
+    for (int q = 1; q < TP; q++)
+        if (e == q) r = a[q];
+    return r;
+}
+
 // Cut the cell by a plane known to remove exactly the vertex slots rem[].  The plane gets an id; every edge
 // x->y of a removed triangle whose neighbour across it is kept lies on the boundary of the removed region and
-// becomes a new triangle (x, y, p) in the lowest free slot.  Adjacency: across x->y the kept neighbour (whose
-// pointer is redirected to the new triangle), across y->p the new triangle starting at y, across p->x the
-// new triangle ending at x.  newm[] returns the new slots.  Returns 0 or a CAP_* code.
+// becomes a new triangle (x, y, p); the k-th boundary edge takes the k-th lowest free slot.  Adjacency: across
+// x->y the kept neighbour (whose pointer is redirected to the new triangle), across y->p the new triangle
+// starting at y, across p->x the new triangle ending at x.  newm[] returns the new slots.  Returns 0 or a CAP_*
+// code.  Each per-slot step is written once (loops over chunks and over boundary ranks), which keeps the
+// kernel's instruction footprint small.
 template <typename CT, int TP>
 __device__ int apply_cut(WarpSmem<CT, TP>& S, CellState<TP>& C, const unsigned* rem, CT nx, CT ny, CT nz, CT h, CT nrm,
                          uint32_t src, int code, unsigned* newm) {
@@ -690,12 +720,14 @@ __device__ int apply_cut(WarpSmem<CT, TP>& S, CellState<TP>& C, const unsigned* 
         S.pnx[p] = nx; S.pny[p] = ny; S.pnz[p] = nz; S.ph[p] = h; S.pnrm[p] = nrm;
         S.psrc[p] = src; S.pcode[p] = (uint8_t)code;
     }
-    // boundary records
+    // boundary records, chunk by chunk (the lane's slot of chunk e is e * 32 + lane)
     int nB = 0;
-#pragma unroll
-    for (int e = 0; e < TP; e++) {
-        if (!rem[e]) continue;
-        const bool mine = (rem[e] >> lane) & 1u;
+    const int nch = (C.hw + 31) >> 5;
+#pragma unroll 1
+    for (int e = 0; e < nch; e++) {
+        const unsigned re = pick<TP>(rem, e);
+        if (!re) continue;
+        const bool mine = (re >> lane) & 1u;
         uint32_t ids[3] = {0u, 0u, 0u}, adj = 0u;
         const uint32_t t = e * 32 + lane;
         if (mine) {
@@ -716,47 +748,53 @@ __device__ int apply_cut(WarpSmem<CT, TP>& S, CellState<TP>& C, const unsigned* 
             }
             nB += __popc(bm);
         }
-        C.vm[e] &= ~rem[e];
     }
+#pragma unroll
+    for (int e = 0; e < TP; e++) C.vm[e] &= ~rem[e];
     __syncwarp();
     if (nB > K::MAXT) return CAP_BOUNDARY;
-    // new triangles into the lowest free slots; link tables by plane id
+    // the new triangles take the nB lowest free slots: masks per chunk (warp-uniform)
+    int before[TP];
     int placed = 0;
-    int myrank[TP];
 #pragma unroll
     for (int e = 0; e < TP; e++) {
-        unsigned fm = ~C.vm[e];
-        int rank = placed + __popc(fm & lt);
-        bool mk = ((fm >> lane) & 1u) && rank < nB;
-        myrank[e] = mk ? rank : -1;
-        if (mk) {
-            uint32_t r = S.bnd[rank];
-            uint32_t x = r & K::IDM, y = (r >> K::IDB) & K::IDM;
-            S.lnk_s[x] = (uint16_t)(e * 32 + lane);
-            S.lnk_e[y] = (uint16_t)(e * 32 + lane);
-        }
-        unsigned nm = __ballot_sync(0xffffffffu, mk);
+        const unsigned fm = ~C.vm[e];
+        before[e] = placed;
+        const unsigned nm = lowest_set_bits(fm, nB - placed);
         newm[e] = nm;
-        C.vm[e] |= nm;
-        if (nm) C.hw = max(C.hw, e * 32 + 32 - __clz(nm));
         placed += __popc(fm);
     }
     if (placed < nB) return CAP_TRIS;
+    // boundary rank r -> its slot; link tables by plane id
+#pragma unroll 1
+    for (int r = (int)lane; r < nB; r += 32) {
+        int e = 0;
+#pragma unroll
+        for (int q = 1; q < TP; q++)
+            if (r >= before[q]) e = q;
+        const uint32_t t = (uint32_t)(e * 32 + nth_set_bit(~pick<TP>(C.vm, e), r - before[e]));
+        const uint32_t rec = S.bnd[r];
+        S.lnk_s[rec & K::IDM] = (uint16_t)t;
+        S.lnk_e[(rec >> K::IDB) & K::IDM] = (uint16_t)t;
+    }
     __syncwarp();
+#pragma unroll 1
+    for (int r = (int)lane; r < nB; r += 32) {
+        const uint32_t rec = S.bnd[r];
+        const uint32_t x = rec & K::IDM, y = (rec >> K::IDB) & K::IDM;
+        const uint32_t n = (rec >> (2 * K::IDB)) & ((1u << K::SB) - 1u), kn = rec >> (2 * K::IDB + K::SB);
+        const uint32_t t = S.lnk_s[x];  // the new triangle whose boundary edge starts at x
+        S.tid[t] = pack<TP>(x, y, (uint32_t)p);
+        S.tadj[t] = adj_pack(n, S.lnk_s[y], S.lnk_e[x]);
+        // redirect the kept neighbour's pointer (fields of one word may be updated by two new triangles)
+        atomicAnd(&S.tadj[n], ~(1023u << (10 * kn)));
+        atomicOr(&S.tadj[n], t << (10 * kn));
+        tri_vertex<CT, TP>(S, t);
+    }
 #pragma unroll
     for (int e = 0; e < TP; e++) {
-        if (myrank[e] >= 0) {
-            const uint32_t t = e * 32 + lane;
-            uint32_t r = S.bnd[myrank[e]];
-            uint32_t x = r & K::IDM, y = (r >> K::IDB) & K::IDM;
-            uint32_t n = (r >> (2 * K::IDB)) & ((1u << K::SB) - 1u), kn = r >> (2 * K::IDB + K::SB);
-            S.tid[t] = pack<TP>(x, y, (uint32_t)p);
-            S.tadj[t] = adj_pack(n, S.lnk_s[y], S.lnk_e[x]);
-            // redirect the kept neighbour's pointer (fields of one word may be updated by two new triangles)
-            atomicAnd(&S.tadj[n], ~(1023u << (10 * kn)));
-            atomicOr(&S.tadj[n], t << (10 * kn));
-            tri_vertex<CT, TP>(S, t);
-        }
+        C.vm[e] |= newm[e];
+        if (newm[e]) C.hw = max(C.hw, e * 32 + 32 - __clz(newm[e]));
     }
     __syncwarp();
     return 0;
@@ -1038,33 +1076,41 @@ __device__ __forceinline__ uint32_t succ_tri(const WarpSmem<CT, TP>& S, uint32_t
     return adj_get(S.tadj[t], (k + 2) % 3);
 }
 
-// Test the lanes' planes against the vertex slots in masks[] and OR the beyond-the-plane slots into outm[].
+// Test the lanes' planes against the vertex slots in masks[] and OR the beyond-the-plane slots into outm[].  One
+// vertex per iteration, against every lane's plane; the slots are taken in increasing order from all chunks by one
+// loop body.
 template <typename P, typename CT, bool EXACT, int TP>
-__device__ __noinline__ void test_slots(const WarpSmem<CT, TP>& S, const unsigned* masks, bool act, CT nx, CT ny, CT nz,
+__device__ __forceinline__ void test_slots(const WarpSmem<CT, TP>& S, unsigned* masks, bool act, CT nx, CT ny, CT nz,
                                            CT h, CT nrm, CT hb, uint32_t src, int code, unsigned* outm,
                                            const P* spos, const Geometry& g, uint32_t self, double* xws,
                                            CellCounters& cc, bool& need_exact, bool& ovf) {
+#pragma unroll 1
+    for (;;) {
+        int s = -1;
 #pragma unroll
-    for (int e = 0; e < TP; e++) {
-        unsigned m = masks[e];
-        while (m) {
-            int l = __ffs(m) - 1;
-            m &= m - 1;
-            int s = e * 32 + l;
-            int sd = act ? side_fast<CT, TP>(S, s, nx, ny, nz, h, nrm, hb) : -1;
-            bool und = act && sd == 0;
-            if (__any_sync(0xffffffffu, und)) {  // every lane calls: resolve may use warp collectives
-                int r = resolve<P, CT, EXACT, TP>(S, s, und, src, code, spos, g, self, xws, cc, need_exact, ovf);
-                if (und) sd = r;
+        for (int e = 0; e < TP; e++)
+            if (s < 0 && masks[e]) {
+                s = e * 32 + __ffs(masks[e]) - 1;
+                masks[e] &= masks[e] - 1;
             }
-            if (sd > 0) outm[e] |= 1u << l;
+        if (s < 0) break;
+        int sd = act ? side_fast<CT, TP>(S, s, nx, ny, nz, h, nrm, hb) : -1;
+        bool und = act && sd == 0;
+        if (__any_sync(0xffffffffu, und)) {  // every lane calls: resolve may use warp collectives
+            int r = resolve<P, CT, EXACT, TP>(S, s, und, src, code, spos, g, self, xws, cc, need_exact, ovf);
+            if (und) sd = r;
+        }
+        if (sd > 0) {
+#pragma unroll
+            for (int e = 0; e < TP; e++)
+                if ((s >> 5) == e) outm[e] |= 1u << (s & 31);
         }
     }
 }
 
 template <typename P, typename CT, bool EXACT, int TP>
-__device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, double* xws, CellCounters& cc,
-                       bool small_box) {
+__device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, double* xws,
+                                    CellCounters& cc, bool small_box) {
     const P* spos = (const P*)A.spos;
     // geometry and sorted index range of the cell's point set
     Geometry g = A.geo;
@@ -1171,20 +1217,15 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         tri_vertex<CT, TP>(S, lane);
     }
     __syncwarp();
-    if (lane < 8) {  // adjacency of the initial octahedron by search
-        uint32_t ids[3];
-        unpack<TP>(S.tid[lane], ids[0], ids[1], ids[2]);
-        uint32_t nb[3] = {0u, 0u, 0u};
-        for (int k = 0; k < 3; k++) {
-            uint32_t x = ids[k], y = ids[(k + 1) % 3];
-            for (int t2 = 0; t2 < 8; t2++) {
-                uint32_t o[3];
-                unpack<TP>(S.tid[t2], o[0], o[1], o[2]);
-                for (int q = 0; q < 3; q++)
-                    if (o[q] == y && o[(q + 1) % 3] == x) nb[k] = (uint32_t)t2;
-            }
-        }
-        S.tadj[lane] = adj_pack(nb[0], nb[1], nb[2]);
+    if (lane < 8) {
+        // adjacency of the initial octahedron: the triangles above list planes (0,2,4), (1,4,2), (0,4,3), (1,3,4),
+        // (0,5,2), (1,2,5), (0,3,5), (1,5,3); across each edge x->y lies the triangle holding y->x, packed as
+        // adj_pack(n0, n1, n2): lane 0 (4,1,2), 1 (3,0,5), 2 (0,3,6), 3 (7,2,1), 4 (6,5,0), 5 (1,4,7), 6 (2,7,4),
+        // 7 (5,6,3)
+        const uint32_t adj = lane == 0 ? adj_pack(4, 1, 2) : lane == 1 ? adj_pack(3, 0, 5) : lane == 2 ? adj_pack(0, 3, 6)
+                           : lane == 3 ? adj_pack(7, 2, 1) : lane == 4 ? adj_pack(6, 5, 0) : lane == 5 ? adj_pack(1, 4, 7)
+                           : lane == 6 ? adj_pack(2, 7, 4) : adj_pack(5, 6, 3);
+        S.tadj[lane] = adj;
     }
     C.vm[0] = 0xFFu;
     C.hw = 8;
@@ -1269,27 +1310,28 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             const CT h = (CT)0.5 * d2;
             const CT nrm = sqrt(d2);
             const CT hb = (CT)16 * u * h;
-            unsigned outm[TP];
+            // test every vertex against the batch's planes; then apply the cutting planes in order, re-testing
+            // only the new vertices against the later planes (a plane that misses a polytope misses every subset)
+            unsigned outm[TP], tmask[TP];
 #pragma unroll
-            for (int e = 0; e < TP; e++) outm[e] = 0u;
-            VT_T0(tt0);
-            if (nact > 0)
-                test_slots<P, CT, EXACT, TP>(S, C.vm, act, dx, dy, dz, h, nrm, hb, j, code, outm, spos, g, self, xws, cc,
-                                         need_exact, ovf);
-            if (!EXACT && __any_sync(0xffffffffu, need_exact)) return RC_NEED_EXACT;
-            if (EXACT && __any_sync(0xffffffffu, ovf)) return VT_ERR_NUMERIC;
+            for (int e = 0; e < TP; e++) { outm[e] = 0u; tmask[e] = nact > 0 ? C.vm[e] : 0u; }
             cc.n_tested += nact;
-            VT_T1(cc, 2, tt0);
-            VT_T0(tk0);
-            // apply the cutting planes in order; the later ones are re-tested against the new vertices only
-            unsigned anyo = 0u;
+            bool any_cut = false;
+            int last = -1;
+            VT_T0(tt0);
+#pragma unroll 1
+            for (;;) {
+                test_slots<P, CT, EXACT, TP>(S, tmask, act && (int)lane > last, dx, dy, dz, h, nrm, hb, j, code, outm,
+                                             spos, g, self, xws, cc, need_exact, ovf);
+                if (!EXACT && __any_sync(0xffffffffu, need_exact)) return RC_NEED_EXACT;
+                if (EXACT && __any_sync(0xffffffffu, ovf)) return VT_ERR_NUMERIC;
+                unsigned anyo = 0u;
 #pragma unroll
-            for (int e = 0; e < TP; e++) anyo |= outm[e];
-            unsigned cutm = __ballot_sync(0xffffffffu, act && anyo);
-            bool any_cut = cutm != 0;
-            while (cutm) {
+                for (int e = 0; e < TP; e++) anyo |= outm[e];
+                const unsigned cutm = __ballot_sync(0xffffffffu, act && (int)lane > last && anyo);
+                if (!cutm) break;
                 const int L = __ffs(cutm) - 1;
-                unsigned rem[TP], newm[TP];
+                unsigned rem[TP];
 #pragma unroll
                 for (int e = 0; e < TP; e++) rem[e] = __shfl_sync(0xffffffffu, outm[e], L);
                 CT px = __shfl_sync(0xffffffffu, dx, L), py = __shfl_sync(0xffffffffu, dy, L),
@@ -1298,24 +1340,17 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
                 uint32_t pj = __shfl_sync(0xffffffffu, j, L);
                 int pc = __shfl_sync(0xffffffffu, code, L);
                 VT_T0(ta0);
-                int rc = apply_cut<CT, TP>(S, C, rem, px, py, pz, ph, pn, pj, pc, newm);
+                int rc = apply_cut<CT, TP>(S, C, rem, px, py, pz, ph, pn, pj, pc, tmask);
                 VT_T1(cc, 6, ta0);
                 if (rc) return rc;
                 cc.n_cut++;
-                const bool later = act && (int)lane > L;
+                any_cut = true;
+                last = L;
 #pragma unroll
                 for (int e = 0; e < TP; e++) outm[e] &= ~rem[e];
-                VT_T0(tr0);
-                test_slots<P, CT, EXACT, TP>(S, newm, later, dx, dy, dz, h, nrm, hb, j, code, outm, spos, g, self, xws,
-                                         cc, need_exact, ovf);
-                VT_T1(cc, 7, tr0);
-                if (!EXACT && __any_sync(0xffffffffu, need_exact)) return RC_NEED_EXACT;
-                if (EXACT && __any_sync(0xffffffffu, ovf)) return VT_ERR_NUMERIC;
-                anyo = 0u;
-#pragma unroll
-                for (int e = 0; e < TP; e++) anyo |= outm[e];
-                cutm = __ballot_sync(0xffffffffu, later && anyo);
             }
+            VT_T1(cc, 2, tt0);
+            VT_T0(tk0);
             if (any_cut) {
                 VT_T0(tb0);
                 R2 = rmax2<CT, TP>(S, C);
@@ -1480,6 +1515,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         co.zz = (float)(vol > 0 ? sg * mzz / vol : (CT)0);
         co.mom2 = (float)m2;
         A.cell[self] = co;
+        if (A.rad) A.rad[self] = (float)sqrt((double)R2) * (1.f + 1e-6f);
         A.face_start[self] = start;
         A.face_count[self] = (uint16_t)nf_total;
         atomicMax(&A.st->max_faces, (unsigned)nf_total);

@@ -817,6 +817,7 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
                 A.face_start[self] = start;
                 A.face_count[self] = (uint16_t)nf;
                 A.cstat[self] = (uint8_t)(CS_DONE | (tc.fp64 != f64_before ? CS_FP64 : 0));
+                if (A.rad) A.rad[self] = sqrtf(C.R2) * (1.f + 1e-6f);
                 atomicMax(&A.st->max_faces, (unsigned)nf);
             }
         }

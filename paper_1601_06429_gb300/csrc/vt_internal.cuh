@@ -113,7 +113,9 @@ struct vt_handle_s {
     uint16_t* face_count;   // [N] sorted order
     uint8_t* cstat;         // [N] sorted order
     uint32_t* exact_list;   // [N]
-    uint32_t* warp_list;    // [N] cells the thread-per-cell kernel hands to the warp kernel
+    uint32_t* warp_list;    // [N] cells the thread-per-cell kernel hands to the warp kernel (or the owned cells)
+    int64_t n_owned;        // cells are computed for input rows [0, n_owned) only (N: all)
+    float* rad;             // [N] sorted order: bound of each computed cell's largest vertex distance
     double* dens_sorted;    // [N] sorted order
     int dens_ready;
     uint64_t* keys;         // [N] Morton keys (sort)

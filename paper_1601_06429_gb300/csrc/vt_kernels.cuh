@@ -26,6 +26,7 @@ int launch_key_batched(const void* pos, int dtype, int64_t N, const Geometry* sg
                        uint64_t* key, uint32_t* idx, DevStatus* st, cudaStream_t s);
 int launch_set_ids(const int64_t* soff, int n_sets, int64_t N, uint32_t* setid, cudaStream_t s);
 int launch_gather_u32(const uint32_t* src, const uint32_t* perm, int64_t N, uint32_t* dst, cudaStream_t s);
+int launch_owned_list(const uint32_t* inv, int64_t n_owned, uint32_t* list, DevStatus* st, cudaStream_t s);
 void tree_layout(int64_t N, Tree& t);
 int launch_tree(const void* spos, int dtype, int64_t N, Tree& t, cudaStream_t s);
 
@@ -59,6 +60,11 @@ struct ClipArgs {
     // batched sets: per-set clipping configuration (k_target in the low 16 bits, bit 16: thread-per-cell
     // kernel first), or NULL for the handle's parameters
     const int32_t* set_cfg;
+    // list_given: warp_list already holds the cells to compute (st->n_warp_cells of them; the other particles
+    // are candidates only) and no thread-per-cell kernel runs
+    int list_given;
+    // per-cell radius (sorted order): an upper bound of the largest vertex distance of the final cell, or NULL
+    float* rad;
 };
 int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s);
 int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
@@ -80,6 +86,7 @@ size_t exact_ws_doubles_per_warp();
 
 // post-processing (vt_post.cu)
 int launch_out_vol(const CellOut* cell, const uint32_t* perm, int64_t N, void* vol, int dtype, cudaStream_t s);
+int launch_out_rad(const float* rad, const uint32_t* perm, int64_t N, void* out, int dtype, cudaStream_t s);
 int launch_cell_flags(const uint8_t* cstat, const uint32_t* perm, int64_t N, uint8_t* out, cudaStream_t s);
 int launch_density(const CellOut* cell, const void* spos, int dtype, const uint32_t* perm, int64_t N,
                     double* dens_sorted, void* dens, cudaStream_t s);

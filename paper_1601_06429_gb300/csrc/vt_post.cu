@@ -30,6 +30,20 @@ int launch_out_vol(const CellOut* cell, const uint32_t* perm, int64_t N, void* v
     return 1;
 }
 
+template <typename T>
+__global__ void k_out_rad(const float* __restrict__ rad, const uint32_t* __restrict__ perm, int64_t N,
+                          T* __restrict__ out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) out[perm[k]] = (T)rad[k];
+}
+
+int launch_out_rad(const float* rad, const uint32_t* perm, int64_t N, void* out, int dtype, cudaStream_t s) {
+    unsigned nb = (unsigned)((N + 255) / 256);
+    if (dtype == VT_F32) k_out_rad<float><<<nb, 256, 0, s>>>(rad, perm, N, (float*)out);
+    else k_out_rad<double><<<nb, 256, 0, s>>>(rad, perm, N, (double*)out);
+    return 1;
+}
+
 // which cells needed a fallback, in input order: bit 0 an FP64 re-decision, bit 1 the exact kernel
 __global__ void k_cell_flags(const uint8_t* __restrict__ cstat, const uint32_t* __restrict__ perm, int64_t N,
                              uint8_t* __restrict__ out) {
@@ -51,7 +65,8 @@ __global__ void k_density(const CellOut* __restrict__ cell, const P* __restrict_
                           T* __restrict__ dens) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    double d = (double)spos[k].w / cell[k].vol;
+    const double v = cell[k].vol;
+    double d = v > 0.0 ? (double)spos[k].w / v : 0.0;  // a particle whose cell was not computed (ghost): 0
     dens_sorted[k] = d;
     if (dens) dens[perm[k]] = (T)d;
 }

@@ -128,6 +128,19 @@ int launch_gather_u32(const uint32_t* src, const uint32_t* perm, int64_t N, uint
     return 1;
 }
 
+// the sorted indices of the owned particles (input rows 0 .. n_owned-1) as the clipping kernel's cell list, and
+// its length
+__global__ void k_owned_list(const uint32_t* __restrict__ inv, int64_t n_owned, uint32_t* __restrict__ list,
+                             DevStatus* st) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_owned) list[k] = inv[k];
+    if (k == 0) st->n_warp_cells = (unsigned)n_owned;
+}
+int launch_owned_list(const uint32_t* inv, int64_t n_owned, uint32_t* list, DevStatus* st, cudaStream_t s) {
+    k_owned_list<<<(unsigned)((n_owned + 255) / 256), 256, 0, s>>>(inv, n_owned, list, st);
+    return 1;
+}
+
 // ---------------------------------------------------------------- scan
 // exclusive scan, blocks of 1024 threads x 4 items, recursive over block sums
 template <typename TI, typename TO>

@@ -81,6 +81,10 @@ def test_build_rejects_bad_arguments_without_device_work(lib):
     p = binding.vt_default_params()
     p.k_target = 2
     assert lib.vt_build(ctypes.byref(h), fake, 0, None, 10, lo, hi, 1, ctypes.byref(p), None) == binding.VT_ERR_INVALID
+    # owned builds: 1 <= n_owned <= N
+    assert lib.vt_build_owned(ctypes.byref(h), fake, 0, None, 10, 0, lo, hi, 1, None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_build_owned(ctypes.byref(h), fake, 0, None, 10, 11, lo, hi, 1, None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_build_owned(None, fake, 0, None, 10, 5, lo, hi, 1, None, None) == binding.VT_ERR_INVALID
     # FP32 filter needs a box length representable in FP32
     p = binding.vt_default_params()
     odd = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
@@ -148,6 +152,7 @@ def test_calls_reject_null_handle(lib):
     assert lib.vt_cells(None, None, None, None, None) == binding.VT_ERR_INVALID
     assert lib.vt_density(None, None) == binding.VT_ERR_INVALID
     assert lib.vt_cell_flags(None, None) == binding.VT_ERR_INVALID
+    assert lib.vt_cell_radius(None, None) == binding.VT_ERR_INVALID
     assert lib.vt_gradient(None, None) == binding.VT_ERR_INVALID
     assert lib.vt_grid_density(None, 8, 1, None) == binding.VT_ERR_INVALID
     assert lib.vt_backward(None, None, 0.0, None) == binding.VT_ERR_INVALID
