@@ -406,18 +406,21 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     xd = torch.from_numpy(x).to(dev)
     w = torch.from_numpy(np.random.default_rng(4).random(N).astype(np.float32)).to(dev)  # dL/dV weights
-    vol = torch.empty(N, dtype=torch.float32, device=dev)
-    dens = torch.empty(N, dtype=torch.float32, device=dev)
-    grad = torch.empty(N, 3, dtype=torch.float32, device=dev)
-    off = torch.empty(N + 1, dtype=torch.int64, device=dev)
-    ids = torch.empty(24 * N, dtype=torch.int32, device=dev)
-    grid = torch.empty(G, G, G, dtype=torch.float32, device=dev) if G else None
-    dpos = torch.empty(N, 3, dtype=torch.float32, device=dev)
+    def outputs():
+        """Device buffers of one step's outputs."""
+        return dict(vol=torch.empty(N, dtype=torch.float32, device=dev),
+                    dens=torch.empty(N, dtype=torch.float32, device=dev),
+                    grad=torch.empty(N, 3, dtype=torch.float32, device=dev),
+                    off=torch.empty(N + 1, dtype=torch.int64, device=dev),
+                    ids=torch.empty(24 * N, dtype=torch.int32, device=dev),
+                    grid=torch.empty(G, G, G, dtype=torch.float32, device=dev) if G else None,
+                    dpos=torch.empty(N, 3, dtype=torch.float32, device=dev))
+
+    out0 = outputs()
     stats = []
     marks = []  # per timed step: events after the forward (build, cells, density, gradient), grid, backward
 
-    def step(pos_dev, mark=False):
-        nonlocal ids
+    def step(pos_dev, mark=False, o=out0):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if mark else None
         if ev:
             ev[0].record(stream)
@@ -426,18 +429,18 @@ def run_ours(args):
         else:
             h = vt.vt_build_batched(pos_dev, set_off, boxes, precision=args.precision, set_k=set_k, set_tpc=set_tpc)
         nnz = vt.vt_cells(h)
-        if nnz > ids.numel():
-            ids = torch.empty(int(nnz * 1.2), dtype=torch.int32, device=dev)
-        vt.vt_cells(h, vol, off, ids)
-        vt.vt_density(h, dens)
-        vt.vt_gradient(h, grad)
+        if nnz > o["ids"].numel():
+            o["ids"] = torch.empty(int(nnz * 1.2), dtype=torch.int32, device=dev)
+        vt.vt_cells(h, o["vol"], o["off"], o["ids"])
+        vt.vt_density(h, o["dens"])
+        vt.vt_gradient(h, o["grad"])
         if ev:
             ev[1].record(stream)
         if G:
-            vt.vt_grid_density(h, G, 1, grid)
+            vt.vt_grid_density(h, G, 1, o["grid"])
         if ev:
             ev[2].record(stream)
-        vt.vt_backward(h, w, 0.0, dpos)
+        vt.vt_backward(h, w, 0.0, o["dpos"])
         if ev:
             ev[3].record(stream)
             marks.append(ev)
@@ -499,6 +502,9 @@ def run_ours(args):
         del gv
 
     # ---------------- end to end through the ABI with host buffers
+    # Every step copies its positions from pinned host memory (H2D stream), computes on the main stream and copies
+    # every output back to pinned host memory (D2H stream).  Two sets of device buffers alternate, so that a step's
+    # output copies run while the next step computes; events order each buffer's reuse.
     xh = torch.from_numpy(x).pin_memory()
     outs_h = dict(vol=torch.empty(N, dtype=torch.float32).pin_memory(),
                   dens=torch.empty(N, dtype=torch.float32).pin_memory(),
@@ -506,42 +512,62 @@ def run_ours(args):
                   off=torch.empty(N + 1, dtype=torch.int64).pin_memory(),
                   grid=torch.empty(G, G, G, dtype=torch.float32).pin_memory() if G else None,
                   dpos=torch.empty(N, 3, dtype=torch.float32).pin_memory())
-    ids_h = torch.empty(ids.numel(), dtype=torch.int32).pin_memory()
-    xd2 = torch.empty_like(xd)
+    ids_h = torch.empty(out0["ids"].numel(), dtype=torch.int32).pin_memory()
+    bufs = [dict(x=torch.empty_like(xd), o=out0), dict(x=torch.empty_like(xd), o=outputs())]
+    s_h2d = torch.cuda.Stream(device=dev)
+    s_d2h = torch.cuda.Stream(device=dev)
+    for b in bufs:
+        b["in"] = torch.cuda.Event()      # positions on the device
+        b["done"] = torch.cuda.Event()    # the step that used this buffer has computed its outputs
+        b["copied"] = torch.cuda.Event()  # its outputs are back on the host
+        b["done"].record(stream)
+        b["copied"].record(stream)
 
-    def copy_out(n):
-        outs_h["vol"].copy_(vol, non_blocking=True)
-        outs_h["dens"].copy_(dens, non_blocking=True)
-        outs_h["grad"].copy_(grad, non_blocking=True)
-        outs_h["off"].copy_(off, non_blocking=True)
-        if G:
-            outs_h["grid"].copy_(grid, non_blocking=True)
-        outs_h["dpos"].copy_(dpos, non_blocking=True)
-        ids_h[:n].copy_(ids[:n], non_blocking=True)
+    def copy_out(o, n):
+        nonlocal ids_h
+        if n > ids_h.numel():
+            ids_h = torch.empty(int(n * 1.2), dtype=torch.int32).pin_memory()
+        for k in ("vol", "dens", "grad", "off", "dpos") + (("grid",) if G else ()):
+            outs_h[k].copy_(o[k], non_blocking=True)
+        ids_h[:n].copy_(o["ids"][:n], non_blocking=True)
 
-    def e2e_step():
-        xd2.copy_(xh, non_blocking=True)
-        n = step(xd2)
-        copy_out(n)
+    def e2e_step(k):
+        b = bufs[k % 2]
+        with torch.cuda.stream(s_h2d):
+            s_h2d.wait_event(b["done"])  # the step two back has read these positions
+            b["x"].copy_(xh, non_blocking=True)
+            b["in"].record(s_h2d)
+        stream.wait_event(b["in"])
+        stream.wait_event(b["copied"])  # the outputs two steps back are on the host
+        n = step(b["x"], o=b["o"])
+        b["done"].record(stream)
+        with torch.cuda.stream(s_d2h):
+            s_d2h.wait_event(b["done"])
+            copy_out(b["o"], n)
+            b["copied"].record(s_d2h)
         return n
 
-    n = e2e_step()
+    n = e2e_step(0)
     torch.cuda.synchronize()
     barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        n = e2e_step()
+    s_h2d.wait_event(e0)
+    for k in range(args.steps):
+        n = e2e_step(k)
+    stream.wait_stream(s_d2h)
     e1.record(stream)
     torch.cuda.synchronize()
     te_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     e2e_value = ws * N * args.steps / (te_ms / 1000.0)
     h2d = N * 12
     d2h = N * 4 + N * 4 + N * 12 + (N + 1) * 8 + G ** 3 * 4 + N * 12 + n * 4
-    # the same copies alone, on the same buffers and stream: the part of the e2e step that is host<->device
+    # the same copies alone, on one stream: the host<->device part of the e2e step
     e0.record(stream)
     for _ in range(args.steps):
-        xd2.copy_(xh, non_blocking=True)
-        copy_out(n)
+        bufs[0]["x"].copy_(xh, non_blocking=True)
+        copy_out(out0, n)
     e1.record(stream)
     torch.cuda.synchronize()
     copy_ms = e0.elapsed_time(e1) / args.steps
@@ -604,7 +630,8 @@ def run_ours(args):
             par = {}
             h = vt.vt_build(xd, None, box[0], box[1], True, args.precision)
             nnz_last = vt.vt_cells(h)
-            out = dict(vol=host(vol), dens=host(dens), grad=host(grad), off=host(off), ids=host(ids[:nnz_last]))
+            out = dict(vol=host(out0["vol"]), dens=host(out0["dens"]), grad=host(out0["grad"]), off=host(out0["off"]),
+                       ids=host(out0["ids"][:nnz_last]))
             par[args.precision] = parity_report(x, L, timer.trees[0], out, vt.cell_flags(h).cpu().numpy())
             vt.vt_destroy(h)
             other = "plain64" if args.precision == "filter32" else "filter32"

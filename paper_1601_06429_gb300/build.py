@@ -42,7 +42,9 @@ def _compile(src: str, verbose: bool) -> str:
         os.path.join(HERE, "..", "include", "vt_gb300.h")]
     if not _stale(obj, deps):
         return obj
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj + ".tmp"]
+    # VT_NVCC_FLAGS: extra flags for diagnostic builds (e.g. -DVT_PHASE_TIMERS); rebuild with force=True
+    extra = os.environ.get("VT_NVCC_FLAGS", "").split()
+    cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -785,6 +785,19 @@ int vt_probe_fp64_tflops(double* tflops, void* stream) { return probe_fma<true>(
 
 int vt_debug_fail_alloc(int nth) { return g_fail_alloc.exchange(nth > 0 ? nth : 0); }
 
+#ifdef VT_PHASE_TIMERS
+// builds with per-phase cycle counters only (not declared in the public header): the counters of the handle's
+// last clipping launch (synchronises)
+int vt_debug_phase_cycles(vt_handle h, unsigned long long* out10) {
+    if (!h || !out10) return VT_ERR_INVALID;
+    DevStatus d;
+    int rc = cuda_rc(cudaMemcpyAsync(&d, h->dstat, sizeof(d), cudaMemcpyDeviceToHost, h->stream));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    if (!rc) memcpy(out10, d.t_phase, sizeof(d.t_phase));
+    return rc;
+}
+#endif
+
 int vt_last_error_detail(int* particle) {
     if (particle) *particle = g_last_particle;
     return g_last_detail;

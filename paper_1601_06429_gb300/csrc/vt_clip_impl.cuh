@@ -543,7 +543,8 @@ __device__ __forceinline__ bool in_mask(const unsigned* m, uint32_t n) {
 struct CellCounters {
     unsigned n_cut, n_tested, n_passes, n_fp64, n_exact, n_zero, n_collect, n_collected;
 #ifdef VT_PHASE_TIMERS
-    unsigned long long t[10];  // cycles: collect, sort, test, cut, emit, total, apply_cut, retest, box, inf-bound tests
+    unsigned long long t[10];  // cycles: collect, sort, plane tests, candidate batches, emit, total, apply_cut, -, box,
+                               // undecided tests on start-box vertices (count)
 #endif
 };
 
@@ -1318,11 +1319,13 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             cc.n_tested += nact;
             bool any_cut = false;
             int last = -1;
-            VT_T0(tt0);
+            VT_T0(tk0);
 #pragma unroll 1
             for (;;) {
+                VT_T0(tt0);
                 test_slots<P, CT, EXACT, TP>(S, tmask, act && (int)lane > last, dx, dy, dz, h, nrm, hb, j, code, outm,
                                              spos, g, self, xws, cc, need_exact, ovf);
+                VT_T1(cc, 2, tt0);
                 if (!EXACT && __any_sync(0xffffffffu, need_exact)) return RC_NEED_EXACT;
                 if (EXACT && __any_sync(0xffffffffu, ovf)) return VT_ERR_NUMERIC;
                 unsigned anyo = 0u;
@@ -1349,8 +1352,6 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
 #pragma unroll
                 for (int e = 0; e < TP; e++) outm[e] &= ~rem[e];
             }
-            VT_T1(cc, 2, tt0);
-            VT_T0(tk0);
             if (any_cut) {
                 VT_T0(tb0);
                 R2 = rmax2<CT, TP>(S, C);
