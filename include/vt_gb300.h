@@ -29,9 +29,9 @@
  *     no device trap crosses this boundary; errors detected on the device are
  *     recorded in the handle and returned by the next call that synchronises
  *     (vt_build, the size query of vt_cells, vt_status).
- *   - Work is enqueued on the stream given to vt_build.  vt_build returns after
- *     one synchronisation (it reads a few status words back); the other calls
- *     are asynchronous unless stated.
+ *   - Work is enqueued on the stream given to vt_build.  vt_build synchronises
+ *     that stream to read a few status words back (and to grow the facet pool
+ *     when a set needs more); the other calls are asynchronous unless stated.
  *   - A handle is not thread-safe; distinct handles are independent.
  */
 #ifndef VT_GB300_H
@@ -392,8 +392,19 @@ int vt_debug_fail_alloc(int nth);
 /* vt_error_string -- static description of a VT_* code. */
 const char *vt_error_string(int code);
 
-/* vt_destroy -- frees the handle and its workspace (NULL is ignored). */
+/*
+ * vt_destroy -- frees the handle and its workspace (NULL is ignored).  Asynchronous: the workspace goes back to
+ * the library's memory pool in order on the handle's stream, after the work already enqueued there.
+ */
 void vt_destroy(vt_handle h);
+
+/*
+ * vt_release_memory -- handle workspaces come from a stream-ordered memory pool per device that the library
+ * creates on first use (cudaMallocFromPoolAsync / cudaFreeAsync on the handle's stream), which keeps freed memory
+ * for the next build instead of returning it to the device; this call synchronises the current device and gives
+ * the pool's unused memory back.  Returns VT_OK or VT_ERR_CUDA.  (Not part of the paper's method.)
+ */
+int vt_release_memory(void);
 
 #ifdef __cplusplus
 }

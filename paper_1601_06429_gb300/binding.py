@@ -134,6 +134,8 @@ def load_library(path: str = LIB_PATH):
     lib.vt_error_string.restype = ctypes.c_char_p
     lib.vt_destroy.argtypes = [P]
     lib.vt_destroy.restype = None
+    lib.vt_release_memory.argtypes = []
+    lib.vt_release_memory.restype = i32
     _lib = lib
     return lib
 
@@ -509,6 +511,11 @@ def vt_destroy(h: Handle) -> None:
     if h is not None and h.ptr is not None and h.ptr.value:
         load_library().vt_destroy(h.ptr)
         h.ptr = None
+
+
+def vt_release_memory() -> None:
+    """Give the unused memory of the library's workspace pool on the current device back (synchronises)."""
+    _check(load_library().vt_release_memory(), "vt_release_memory")
 
 
 VT_NOALLOC_MAX_N = 8192

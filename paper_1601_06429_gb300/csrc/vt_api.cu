@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <new>
 
 #include "vt_internal.cuh"
@@ -34,21 +35,66 @@ bool injected_failure() {
     return false;
 }
 
+// Handle workspaces come from a stream-ordered memory pool per device that the library owns: allocations and
+// frees are ordered on the handle's stream (a free does not synchronise the device, so work of other streams,
+// e.g. copies of a previous step's outputs, keeps running), and freed memory stays in the pool for the next
+// build until vt_release_memory returns it.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+cudaMemPool_t device_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;  // keep freed memory for reuse
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
+// one workspace allocation on the handle's stream from the device's pool (nullptr on failure)
+void* pool_alloc(size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = device_pool();
+    void* p = nullptr;
+    if (!pool || cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pool_free(void* p, cudaStream_t s) {
+    if (p && cudaFreeAsync(p, s) != cudaSuccess) cudaGetLastError();
+}
+
 struct Alloc {
+    cudaStream_t s = nullptr;
     bool failed = false;
     template <typename T>
     T* get(size_t count) {
         if (count == 0) count = 1;
-        void* p = nullptr;
         if (injected_failure()) {
             failed = true;
             return nullptr;
         }
-        if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
-            cudaGetLastError();
-            failed = true;
-            return nullptr;
-        }
+        void* p = pool_alloc(count * sizeof(T), s);
+        if (!p) failed = true;
         return (T*)p;
     }
 };
@@ -62,7 +108,7 @@ void free_handle(vt_handle h) {
                     h->keys, h->keys_alt, h->vals_alt, h->cnt_in, h->sset, h->sgeo, h->soff, h->set_in, h->warp_list,
                     h->set_cfg, h->gacc, h->gretry, h->gcnt};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) pool_free(p, h->stream);
     delete h;
 }
 
@@ -146,12 +192,9 @@ int run_clip(vt_handle h) {
         uint64_t need = h->hstat.face_next + (uint64_t)h->N * 4;
         uint64_t cap = h->face_cap * 2 > need ? h->face_cap * 2 : need;
         if (cap > 0xF0000000ull) return VT_ERR_CAPACITY;
-        cudaFree(h->faces);
-        h->faces = nullptr;
-        if (cudaMalloc((void**)&h->faces, cap * sizeof(Face)) != cudaSuccess) {
-            cudaGetLastError();
-            return VT_ERR_OOM;
-        }
+        pool_free(h->faces, s);
+        h->faces = (Face*)pool_alloc(cap * sizeof(Face), s);
+        if (!h->faces) return VT_ERR_OOM;
         h->face_cap = cap;
         h->hstat.error = 0;
     }
@@ -264,6 +307,7 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
     if (h->sm_count <= 0) h->sm_count = 1;
 
     Alloc A;
+    A.s = h->stream;
     size_t psz = dtype == VT_F32 ? sizeof(float4) : sizeof(dpt4);
     h->spos = A.get<unsigned char>(N * psz);
     h->keys = A.get<uint64_t>(N);
@@ -566,10 +610,9 @@ int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t*
     if (nbr_off || nbr_id) {
         int64_t* off = nbr_off;
         if (!off) {
-            if (!h->nbr_off_cache && cudaMalloc((void**)&h->nbr_off_cache, (h->N + 1) * sizeof(int64_t)) != cudaSuccess) {
-                cudaGetLastError();
-                h->nbr_off_cache = nullptr;
-                return VT_ERR_OOM;
+            if (!h->nbr_off_cache) {
+                h->nbr_off_cache = (int64_t*)pool_alloc((h->N + 1) * sizeof(int64_t), s);
+                if (!h->nbr_off_cache) return VT_ERR_OOM;
             }
             off = h->nbr_off_cache;
         }
@@ -633,11 +676,9 @@ int vt_grid_density(vt_handle h, int G, int S, void* grid) {
 namespace {
 int ensure_retry(vt_handle h) {
     if (h->gretry) return VT_OK;
-    if (cudaMalloc((void**)&h->gretry, (size_t)GRID_RETRY_CAP * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc((void**)&h->gcnt, 16 * sizeof(unsigned)) != cudaSuccess) {
-        cudaGetLastError();
-        return VT_ERR_OOM;
-    }
+    h->gretry = (int4*)pool_alloc((size_t)GRID_RETRY_CAP * sizeof(int4), h->stream);
+    h->gcnt = (unsigned*)pool_alloc(16 * sizeof(unsigned), h->stream);
+    if (!h->gretry || !h->gcnt) return VT_ERR_OOM;
     return VT_OK;
 }
 }  // namespace
@@ -659,13 +700,10 @@ int vt_grid_density_volume(vt_handle h, int G, void* grid) {
     if (rc) return rc;
     const int64_t n = (int64_t)G * G * G;
     if (h->gacc_n < n) {
-        if (h->gacc) cudaFree(h->gacc);
-        h->gacc = nullptr;
+        pool_free(h->gacc, h->stream);
         h->gacc_n = 0;
-        if (cudaMalloc((void**)&h->gacc, n * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            return VT_ERR_OOM;
-        }
+        h->gacc = (double*)pool_alloc(n * sizeof(double), h->stream);
+        if (!h->gacc) return VT_ERR_OOM;
         h->gacc_n = n;
     }
     rc = ensure_retry(h);
@@ -820,8 +858,19 @@ const char* vt_error_string(int code) {
 
 void vt_destroy(vt_handle h) {
     if (!h) return;
-    cudaStreamSynchronize(h->stream);
-    free_handle(h);
+    free_handle(h);  // frees ordered after the handle's pending work on its stream
+}
+
+int vt_release_memory(void) {
+    cudaMemPool_t pool = device_pool();
+    if (!pool) return VT_ERR_CUDA;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceSynchronize() != cudaSuccess) {  // frees still pending on a stream return after their work
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    return cuda_rc(cudaMemPoolTrimTo(pool, 0));
 }
 
 }  // extern "C"
