@@ -1078,35 +1078,36 @@ __device__ __forceinline__ uint32_t succ_tri(const WarpSmem<CT, TP>& S, uint32_t
 }
 
 // Test the lanes' planes against the vertex slots in masks[] and OR the beyond-the-plane slots into outm[].  One
-// vertex per iteration, against every lane's plane; the slots are taken in increasing order from all chunks by one
-// loop body.
+// vertex per iteration, against every lane's plane; the chunks of 32 slots are taken in turn by one loop (one
+// copy of the per-vertex body).  masks[] is consumed.
 template <typename P, typename CT, bool EXACT, int TP>
 __device__ __forceinline__ void test_slots(const WarpSmem<CT, TP>& S, unsigned* masks, bool act, CT nx, CT ny, CT nz,
                                            CT h, CT nrm, CT hb, uint32_t src, int code, unsigned* outm,
                                            const P* spos, const Geometry& g, uint32_t self, double* xws,
                                            CellCounters& cc, bool& need_exact, bool& ovf) {
 #pragma unroll 1
-    for (;;) {
-        int s = -1;
-#pragma unroll
-        for (int e = 0; e < TP; e++)
-            if (s < 0 && masks[e]) {
-                s = e * 32 + __ffs(masks[e]) - 1;
-                masks[e] &= masks[e] - 1;
+    for (int e = 0; e < TP; e++) {
+        unsigned m = pick<TP>(masks, e);
+        if (!m) continue;
+        unsigned o = 0u;
+        do {
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const int s = e * 32 + l;
+            int sd = act ? side_fast<CT, TP>(S, s, nx, ny, nz, h, nrm, hb) : -1;
+            const bool und = act && sd == 0;
+            if (__any_sync(0xffffffffu, und)) {  // every lane calls: resolve may use warp collectives
+                const int r = resolve<P, CT, EXACT, TP>(S, s, und, src, code, spos, g, self, xws, cc, need_exact, ovf);
+                if (und) sd = r;
             }
-        if (s < 0) break;
-        int sd = act ? side_fast<CT, TP>(S, s, nx, ny, nz, h, nrm, hb) : -1;
-        bool und = act && sd == 0;
-        if (__any_sync(0xffffffffu, und)) {  // every lane calls: resolve may use warp collectives
-            int r = resolve<P, CT, EXACT, TP>(S, s, und, src, code, spos, g, self, xws, cc, need_exact, ovf);
-            if (und) sd = r;
-        }
-        if (sd > 0) {
+            if (sd > 0) o |= 1u << l;
+        } while (m);
 #pragma unroll
-            for (int e = 0; e < TP; e++)
-                if ((s >> 5) == e) outm[e] |= 1u << (s & 31);
-        }
+        for (int q = 0; q < TP; q++)
+            if (q == e) outm[q] |= o;
     }
+#pragma unroll
+    for (int q = 0; q < TP; q++) masks[q] = 0u;
 }
 
 template <typename P, typename CT, bool EXACT, int TP>
