@@ -928,29 +928,9 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
     const float reach = rad + 4.f * slack;
     const int per = g.periodic && !(qx - reach > g.lof[0] && qx + reach < g.hif[0] && qy - reach > g.lof[1] &&
                                     qy + reach < g.hif[1] && qz - reach > g.lof[2] && qz + reach < g.hif[2]);
-    int sp = 0;
-    int top = t.levels;
-    {
-        int64_t nt = t.count[top];
-        bool hit = false;
-        const int64_t span_top = (int64_t)1 << (5 * top);
-        if ((int64_t)lane < nt && lane * span_top < shi && (lane + 1) * span_top > slo) {
-            float4 lo = t.lo[t.off[top] + lane], hi = t.hi[t.off[top] + lane];
-            float dx = fmaxf(axis_gap(qx, lo.x, hi.x, g.Lf[0], per) - slack, 0.f);
-            float dy = fmaxf(axis_gap(qy, lo.y, hi.y, g.Lf[1], per) - slack, 0.f);
-            float dz = fmaxf(axis_gap(qz, lo.z, hi.z, g.Lf[2], per) - slack, 0.f);
-            hit = dx * dx + dy * dy + dz * dz <= rad2;
-            if (hit) {
-                float sx = supp_axis(qx, lo.x - slack, hi.x + slack, g.Lf[0], per, bmin[0], bmax[0]);
-                float sy = supp_axis(qy, lo.y - slack, hi.y + slack, g.Lf[1], per, bmin[1], bmax[1]);
-                float sz = supp_axis(qz, lo.z - slack, hi.z + slack, g.Lf[2], per, bmin[2], bmax[2]);
-                if (sx + sy + sz < -stol) hit = false;
-            }
-        }
-        unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (hit) S.stack[__popc(m & lt)] = ((uint32_t)top << 27) | lane;
-        sp = __popc(m);
-    }
+    // the root: a virtual node one level above the top, whose children are the top-level nodes
+    if (lane == 0) S.stack[0] = ((uint32_t)(t.levels + 1) << 27) | 0u;
+    int sp = 1;
     __syncwarp();
     int count = 0;
     while (sp > 0) {
@@ -1555,8 +1535,14 @@ __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
             uint32_t self = EXACT ? A.exact_list[q] : listed ? A.warp_list[q] : q;
             VT_T0(tall);
             const unsigned f64_before = cc.n_fp64;
-            int rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, !EXACT);
-            if (rc == RC_RETRY_BOX) rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, false);
+            // one call site (the cell routine is inlined once): the small start box first, then, if the cell
+            // reached one of its artificial walls, the true walls
+            int rc = 0;
+#pragma unroll 1
+            for (int attempt = 0; attempt < 2; attempt++) {
+                rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, !EXACT && attempt == 0);
+                if (rc != RC_RETRY_BOX) break;
+            }
             VT_T1(cc, 5, tall);
             const bool used64 = __any_sync(0xffffffffu, cc.n_fp64 != f64_before);
             __syncwarp();
