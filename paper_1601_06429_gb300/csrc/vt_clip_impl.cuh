@@ -231,6 +231,26 @@ template <> __device__ __forceinline__ double fromfbits<double>(unsigned long lo
     return __longlong_as_double((long long)b);
 }
 
+// displacement of particle j seen from i without a periodic shift: the shift-free path of DispF, rounded the same way
+template <typename P, typename CT> struct DispPlain;
+template <> struct DispPlain<float4, float> {
+    static __device__ __forceinline__ void get(const float4& pj, const float4& pi, float& dx, float& dy, float& dz) {
+        dx = __fsub_rn(pj.x, pi.x); dy = __fsub_rn(pj.y, pi.y); dz = __fsub_rn(pj.z, pi.z);
+    }
+};
+template <typename P> struct DispPlain<P, double> {
+    static __device__ __forceinline__ void get(const P& pj, const P& pi, double& dx, double& dy, double& dz) {
+        dx = __dsub_rn((double)pj.x, (double)pi.x);
+        dy = __dsub_rn((double)pj.y, (double)pi.y);
+        dz = __dsub_rn((double)pj.z, (double)pi.z);
+    }
+};
+template <> struct DispPlain<dpt4, float> {
+    static __device__ __forceinline__ void get(const dpt4& pj, const dpt4& pi, float& dx, float& dy, float& dz) {
+        dx = (float)__dsub_rn(pj.x, pi.x); dy = (float)__dsub_rn(pj.y, pi.y); dz = (float)__dsub_rn(pj.z, pi.z);
+    }
+};
+
 // displacement of particle j seen from i in precision CT, and the periodic shift used
 template <typename P, typename CT> struct DispF;
 template <> struct DispF<float4, float> {
@@ -947,7 +967,11 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
             int code = 13;
             if (j >= slo && j < shi && (uint32_t)j != self) {
                 P pj = spos[j];
-                DispF<P, CT>::get(pj, pi, g, dx, dy, dz, code);
+                // a search ball inside the periodic box holds no shifted image (an image lies outside the box), and
+                // a point's unshifted distance is at least its minimum-image one: the same points pass the radius
+                // test, with the same displacements, as with the shifts
+                if (per) DispF<P, CT>::get(pj, pi, g, dx, dy, dz, code);
+                else DispPlain<P, CT>::get(pj, pi, dx, dy, dz);
                 d2 = f_fma<CT>(dz, dz, f_fma<CT>(dy, dy, dx * dx));
                 hit = (d2 >= rlo2) && (d2 < rhi2);
                 if (hit) {
