@@ -48,7 +48,8 @@ struct Cap {
     static constexpr int MAXP = TP <= 4 ? 128 : 512;
     static constexpr uint32_t IDM = (1u << IDB) - 1u;
     static constexpr int SB = TP <= 4 ? 7 : 9;            // bits of a vertex slot
-    static constexpr int CAND = TP <= 4 ? 128 : 256;      // candidates per radius pass (a power of two: sort_cand)
+    static constexpr int CAND = 256;                      // candidates per radius pass (a power of two: sort_cand)
+    static constexpr int AIM = TP <= 4 ? 128 : 256;       // the pass sizing aims at 3/4 of this many candidates
     static constexpr int STACK = TP <= 4 ? STACK_CAP : 4 * STACK_CAP;
     static_assert((CAND & (CAND - 1)) == 0, "sort_cand pads the candidates to a power of two up to CAND");
 };
@@ -81,9 +82,7 @@ struct WarpSmem {
     union {
         struct {
             unsigned long long key[K::CAND];  // (|d|^2 as float bits) << 32 | slot
-            CT dx[K::CAND], dy[K::CAND], dz[K::CAND];
-            uint32_t j[K::CAND];
-            uint8_t code[K::CAND];
+            uint32_t j[K::CAND];               // the candidate (its displacement is recomputed when it is used)
         } cd;
         struct {
             uint32_t first[K::MAXP];
@@ -988,9 +987,7 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
             int o = count + __popc(m & lt);
             if (hit && o < Cap<TP>::CAND) {
                 S.u.cd.key[o] = key | (uint32_t)o;
-                S.u.cd.dx[o] = dx; S.u.cd.dy[o] = dy; S.u.cd.dz[o] = dz;
                 S.u.cd.j[o] = (uint32_t)j;
-                S.u.cd.code[o] = (uint8_t)code;
             }
             if (hit) {
                 unsigned long long bb = fbits<CT>(d2);
@@ -1302,8 +1299,9 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
                 uint32_t slot = (uint32_t)(key & 0xffffffffu);
                 kf = __uint_as_float((uint32_t)(key >> 32));
                 j = S.u.cd.j[slot];
-                code = S.u.cd.code[slot];
-                dx = S.u.cd.dx[slot]; dy = S.u.cd.dy[slot]; dz = S.u.cd.dz[slot];
+                // the displacement exactly as the search computed it (the same rounding; no shift for a point
+                // the search found without one)
+                DispF<P, CT>::get(spos[j], pi, g, dx, dy, dz, code);
             }
             // security radius: a plane at |d| >= 2R cannot cut; keys only grow along the list
             const bool far = valid && (CT)kf * ((CT)1 - (CT)8 * u) > (CT)4 * R2;
@@ -1384,7 +1382,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
                 float rh = sqrtf((float)rhi2), rl = sqrtf((float)rlo2);
                 float shell = rh * rh * rh - rl * rl * rl;
                 if (shell > 0.f) {
-                    float r = cbrtf(rh * rh * rh + 0.75f * K::CAND * shell / (float)cnt);
+                    float r = cbrtf(rh * rh * rh + 0.75f * K::AIM * shell / (float)cnt);
                     lim = fminf(lim, fmaxf(r * r, 1.21f * (float)rhi2));
                 }
             }
