@@ -49,7 +49,6 @@ struct Cap {
     static constexpr uint32_t IDM = (1u << IDB) - 1u;
     static constexpr int SB = TP <= 4 ? 7 : 9;            // bits of a vertex slot
     static constexpr int CAND = 256;                      // candidates per radius pass (a power of two: sort_cand)
-    static constexpr int AIM = TP <= 4 ? 128 : 256;       // the pass sizing aims at 3/4 of this many candidates
     static constexpr int STACK = TP <= 4 ? STACK_CAP : 4 * STACK_CAP;
     static_assert((CAND & (CAND - 1)) == 0, "sort_cand pads the candidates to a power of two up to CAND");
 };
@@ -1382,7 +1381,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
                 float rh = sqrtf((float)rhi2), rl = sqrtf((float)rlo2);
                 float shell = rh * rh * rh - rl * rl * rl;
                 if (shell > 0.f) {
-                    float r = cbrtf(rh * rh * rh + 0.75f * K::AIM * shell / (float)cnt);
+                    float r = cbrtf(rh * rh * rh + 0.75f * K::CAND * shell / (float)cnt);
                     lim = fminf(lim, fmaxf(r * r, 1.21f * (float)rhi2));
                 }
             }
