@@ -423,7 +423,7 @@ def run_ours(args):
     stats = []
     marks = []  # per timed step: events after the forward (build, cells, density, gradient), grid, backward
 
-    def step(pos_dev, mark=False, o=out0, after_build=None):
+    def step(pos_dev, mark=False, o=out0):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if mark else None
         if ev:
             ev[0].record(stream)
@@ -431,8 +431,6 @@ def run_ours(args):
             h = vt.vt_build(pos_dev, None, box[0], box[1], True, args.precision)
         else:
             h = vt.vt_build_batched(pos_dev, set_off, boxes, precision=args.precision, set_k=set_k, set_tpc=set_tpc)
-        if after_build is not None:
-            after_build()
         nnz = vt.vt_cells(h)
         if nnz > o["ids"].numel():
             o["ids"] = torch.empty(int(nnz * 1.2), dtype=torch.int32, device=dev)
@@ -507,11 +505,10 @@ def run_ours(args):
         del gv
 
     # ---------------- end to end through the ABI with host buffers
-    # Every step copies its positions from pinned host memory (H2D stream), computes on the main stream and copies
-    # every output back to pinned host memory (D2H stream).  Two sets of device buffers alternate, and a step's
-    # output copies are issued once the next step's vt_build has returned, so that they run beside that step's
-    # output kernels (issued earlier, they queue the build's small status reads behind 1.8 GB on the copy engine);
-    # events order each buffer's reuse.
+    # Every step's positions come from pinned host memory (H2D stream) and every output goes back to pinned host
+    # memory (D2H stream).  Two sets of device buffers alternate: the next step's positions are copied in during
+    # this step, and this step's outputs are copied out during the next one (the library reads its status words
+    # through mapped memory, so its builds never wait behind these copies); events order each buffer's reuse.
     xh = torch.from_numpy(x).pin_memory()
     outs_h = dict(vol=torch.empty(N, dtype=torch.float32).pin_memory(),
                   dens=torch.empty(N, dtype=torch.float32).pin_memory(),
@@ -538,40 +535,37 @@ def run_ours(args):
             outs_h[k].copy_(o[k], non_blocking=True)
         ids_h[:n].copy_(o["ids"][:n], non_blocking=True)
 
-    pending = []  # the previous step's (buffer, facet count), whose outputs are still to be copied
-
-    def flush():
-        while pending:
-            b, n = pending.pop()
-            with torch.cuda.stream(s_d2h):
-                s_d2h.wait_event(b["done"])
-                copy_out(b["o"], n)
-                b["copied"].record(s_d2h)
-
-    def e2e_step(k):
-        b = bufs[k % 2]
+    def copy_in(b):
         with torch.cuda.stream(s_h2d):
             s_h2d.wait_event(b["done"])  # the step two back has read these positions
             b["x"].copy_(xh, non_blocking=True)
             b["in"].record(s_h2d)
+
+    def e2e_step(k, prefetch):
+        b = bufs[k % 2]
+        if prefetch:
+            copy_in(bufs[(k + 1) % 2])  # the next step's positions, during this step
         stream.wait_event(b["in"])
         stream.wait_event(b["copied"])  # the outputs two steps back are on the host
-        n = step(b["x"], o=b["o"], after_build=flush)
+        n = step(b["x"], o=b["o"])
         b["done"].record(stream)
-        pending.append((b, n))
+        with torch.cuda.stream(s_d2h):
+            s_d2h.wait_event(b["done"])
+            copy_out(b["o"], n)
+            b["copied"].record(s_d2h)
         return n
 
-    n = e2e_step(0)
-    flush()
+    copy_in(bufs[0])
+    n = e2e_step(0, False)
     torch.cuda.synchronize()
     barrier(ws)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     s_h2d.wait_event(e0)
+    copy_in(bufs[0])
     for k in range(args.steps):
-        n = e2e_step(k)
-    flush()
+        n = e2e_step(k, k + 1 < args.steps)
     stream.wait_stream(s_d2h)
     e1.record(stream)
     torch.cuda.synchronize()

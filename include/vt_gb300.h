@@ -32,6 +32,11 @@
  *   - Work is enqueued on the stream given to vt_build.  vt_build synchronises
  *     that stream to read a few status words back (and to grow the facet pool
  *     when a set needs more); the other calls are asynchronous unless stated.
+ *     Status words are read through mapped pinned host memory that a small
+ *     kernel on the handle's stream writes, not by a copy: a synchronising
+ *     call never waits for copies that other streams have queued on the copy
+ *     engines.  Each live handle holds one such block (a few hundred bytes,
+ *     reused by later handles).
  *   - A handle is not thread-safe; distinct handles are independent.
  */
 #ifndef VT_GB300_H

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "vt_internal.cuh"
 #include "vt_kernels.cuh"
@@ -99,6 +100,34 @@ struct Alloc {
     }
 };
 
+// Mapped pinned blocks for the status reads, one per live handle, kept for reuse (never returned to the system:
+// a build does not pay for a pinned allocation).
+std::mutex g_map_mu;
+std::vector<DevStatus*> g_map_free;
+
+DevStatus* map_take() {
+    {
+        std::lock_guard<std::mutex> lk(g_map_mu);
+        if (!g_map_free.empty()) {
+            DevStatus* p = g_map_free.back();
+            g_map_free.pop_back();
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(DevStatus), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (DevStatus*)p;
+}
+
+void map_give(DevStatus* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    g_map_free.push_back(p);
+}
+
 void free_handle(vt_handle h) {
     if (!h) return;
     for (int k = 0; k < 4; k++)
@@ -109,6 +138,7 @@ void free_handle(vt_handle h) {
                     h->set_cfg, h->gacc, h->gretry, h->gcnt};
     for (void* p : ptrs)
         if (p) pool_free(p, h->stream);
+    map_give(h->smap);
     delete h;
 }
 
@@ -116,6 +146,41 @@ int cuda_rc(cudaError_t e) {
     if (e == cudaSuccess) return VT_OK;
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? VT_ERR_OOM : VT_ERR_CUDA;
+}
+
+// Status words reach the host through mapped pinned memory: one small block copies them there, and the host reads them
+// after synchronising the handle's stream.  No copy engine takes part, so a status read never waits behind large
+// copies that other streams have in flight (e.g. a previous step's outputs going to the host).
+static_assert(sizeof(DevStatus) % 4 == 0, "status words are copied as 32-bit words");
+__global__ void k_status_copy(const DevStatus* src, DevStatus* dst) {
+    const unsigned* a = (const unsigned*)src;
+    unsigned* b = (unsigned*)dst;
+    for (int k = (int)threadIdx.x; k < (int)(sizeof(DevStatus) / 4); k += blockDim.x) b[k] = a[k];
+}
+// clear every status word, then set the input-validation count and the error to the given values
+__global__ void k_status_reset(DevStatus* st, unsigned invalid_input, int error) {
+    unsigned* w = (unsigned*)st;
+    for (int k = (int)threadIdx.x; k < (int)(sizeof(DevStatus) / 4); k += blockDim.x) w[k] = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->invalid_input = invalid_input;
+        st->error = error;
+    }
+}
+
+// the handle's status words as they stand after its stream's work so far (synchronises the stream)
+int read_status(vt_handle h, DevStatus* out) {
+    DevStatus* dmap = nullptr;
+    if (cudaHostGetDevicePointer((void**)&dmap, h->smap, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return VT_ERR_CUDA;
+    }
+    k_status_copy<<<1, 128, 0, h->stream>>>(h->dstat, dmap);
+    h->n_launches += 1;
+    int rc = cuda_rc(cudaGetLastError());
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    if (!rc) memcpy(out, (const void*)h->smap, sizeof(DevStatus));
+    return rc;
 }
 
 ClipArgs clip_args(vt_handle h) {
@@ -163,16 +228,10 @@ int enqueue_owned(vt_handle h) {
 int run_clip(vt_handle h) {
     cudaStream_t s = h->stream;
     for (int attempt = 0; attempt < 4; attempt++) {
-        // reset the clipping counters (the input-validation count is kept)
-        DevStatus z;
-        memset(&z, 0, sizeof(z));
-        z.invalid_input = h->hstat.invalid_input;
-        z.error = h->hstat.error;
-        int rc = cuda_rc(cudaMemcpyAsync(h->dstat, &z, sizeof(z), cudaMemcpyHostToDevice, s));
-        if (rc) return rc;
-        rc = cuda_rc(cudaStreamSynchronize(s));
-        if (rc) return rc;
-        rc = enqueue_owned(h);
+        // reset the clipping counters (the input-validation count and the error as last read are kept)
+        k_status_reset<<<1, 128, 0, s>>>(h->dstat, h->hstat.invalid_input, h->hstat.error);
+        h->n_launches += 1;
+        int rc = enqueue_owned(h);
         if (rc) return rc;
         ClipArgs a = clip_args(h);
         cudaEventRecord(h->ev[2], s);
@@ -181,9 +240,7 @@ int run_clip(vt_handle h) {
         cudaEventRecord(h->ev[3], s);
         rc = cuda_rc(cudaGetLastError());
         if (rc) return rc;
-        rc = cuda_rc(cudaMemcpyAsync(&h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-        if (rc) return rc;
-        rc = cuda_rc(cudaStreamSynchronize(s));
+        rc = read_status(h, &h->hstat);
         if (rc) return rc;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]) == cudaSuccess) h->t_clip_ms = ms;
@@ -337,6 +394,8 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
     h->tmp_bytes = tb > sb ? tb : sb;
     h->tmp = A.get<unsigned char>(h->tmp_bytes);
     h->dstat = A.get<DevStatus>(1);
+    h->smap = map_take();
+    if (!h->smap) A.failed = true;
     if (n_sets > 0) {
         h->sset = A.get<uint32_t>(N);
         h->set_in = A.get<uint32_t>(N);
@@ -375,8 +434,7 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
         cudaEventRecord(h->ev[1], s);
         rc = cuda_rc(cudaGetLastError());
     }
-    if (!rc) rc = cuda_rc(cudaMemcpyAsync(&h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-    if (!rc) rc = cuda_rc(cudaStreamSynchronize(s));
+    if (!rc) rc = read_status(h, &h->hstat);
     if (!rc) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) == cudaSuccess) h->t_sort_ms = ms;
@@ -599,8 +657,7 @@ int vt_cells(vt_handle h, void* vol, int64_t* nbr_off, int32_t* nbr_id, int64_t*
     if (n_faces_out) {
         if (h->faces_on_device) {
             // once the handle has been rebuilt (perhaps by a replayed graph) the count is read from the device
-            int rc = cuda_rc(cudaMemcpyAsync(&h->hstat, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-            if (!rc) rc = cuda_rc(cudaStreamSynchronize(s));
+            int rc = read_status(h, &h->hstat);
             if (rc) return rc;
             h->n_faces = (int64_t)h->hstat.n_faces;
         }
@@ -730,8 +787,7 @@ int vt_backward(vt_handle h, const void* dL_dV, double dL_dE, void* dL_dpos) {
 int vt_status(vt_handle h, vt_stats* out) {
     if (!h || !out) return VT_ERR_INVALID;
     DevStatus d;
-    int rc = cuda_rc(cudaMemcpyAsync(&d, h->dstat, sizeof(d), cudaMemcpyDeviceToHost, h->stream));
-    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    int rc = read_status(h, &d);
     if (rc) return rc;
     memset(out, 0, sizeof(*out));
     out->n = h->N;
@@ -829,8 +885,7 @@ int vt_debug_fail_alloc(int nth) { return g_fail_alloc.exchange(nth > 0 ? nth : 
 int vt_debug_phase_cycles(vt_handle h, unsigned long long* out10) {
     if (!h || !out10) return VT_ERR_INVALID;
     DevStatus d;
-    int rc = cuda_rc(cudaMemcpyAsync(&d, h->dstat, sizeof(d), cudaMemcpyDeviceToHost, h->stream));
-    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    int rc = read_status(h, &d);
     if (!rc) memcpy(out10, d.t_phase, sizeof(d.t_phase));
     return rc;
 }

@@ -134,6 +134,7 @@ struct vt_handle_s {
     int nbr_ready;
     vt::DevStatus* dstat;   // device
     vt::DevStatus hstat;    // host copy after build
+    vt::DevStatus* smap;    // mapped pinned host block through which the status words are read
     int64_t n_faces;
     int faces_on_device;    // set by vt_rebuild: the facet count is read from the device from then on
     // volume-averaged grid: accumulator, retry list of the larger cell type, counters (retries, failures)
