@@ -48,9 +48,8 @@ struct Cap {
     static constexpr int MAXP = TP <= 4 ? 128 : 512;
     static constexpr uint32_t IDM = (1u << IDB) - 1u;
     static constexpr int SB = TP <= 4 ? 7 : 9;            // bits of a vertex slot
-    static constexpr int CAND = 256;                      // candidates per radius pass (a power of two: sort_cand)
+    static constexpr int CAND = 256;                      // candidates per radius pass
     static constexpr int STACK = TP <= 4 ? STACK_CAP : 4 * STACK_CAP;
-    static_assert((CAND & (CAND - 1)) == 0, "sort_cand pads the candidates to a power of two up to CAND");
 };
 constexpr int CHUNK = 4;
 
@@ -67,17 +66,29 @@ template <> struct Stor<float4> { typedef float T; };
 template <> struct Stor<dpt4> { typedef double T; };
 
 // ------------------------------------------------------------------ shared memory
+// a vertex's position (relative to the site) and the bound of its error, read and written as one record
+template <typename CT> struct Vtx;
+template <> struct __align__(16) Vtx<float> { float x, y, z, ev; };
+template <> struct __align__(32) Vtx<double> { double x, y, z, ev; };
+
+// a plane n.y <= h (n the displacement, or a unit wall normal) as one record; its norm |n| is kept apart
+template <typename CT> struct Pln;
+template <> struct __align__(16) Pln<float> { float x, y, z, h; };
+template <> struct __align__(32) Pln<double> { double x, y, z, h; };
+
 template <typename CT, int TP>
 struct WarpSmem {
     typedef Cap<TP> K;
     // planes that have cut the cell: n.y <= h with |n| = nrm, source particle and image shift
-    CT pnx[K::MAXP], pny[K::MAXP], pnz[K::MAXP], ph[K::MAXP], pnrm[K::MAXP];
+    Pln<CT> pl[K::MAXP];
+    CT pnrm[K::MAXP];
     uint32_t psrc[K::MAXP];
     uint8_t pcode[K::MAXP];  // 0..26 image shift code, 27+w box wall w
     // vertices = triangles of the dual triangulation: packed plane ids, position, error bound, R^2 bound
     uint32_t tid[K::MAXT];
     uint32_t tadj[K::MAXT];  // neighbour slot across edge k (k = 0: a->b, 1: b->c, 2: c->a), 10 bits each
-    CT tx[K::MAXT], ty[K::MAXT], tz[K::MAXT], tev[K::MAXT], trr[K::MAXT];
+    Vtx<CT> tv[K::MAXT];
+    CT trr[K::MAXT];
     union {
         struct {
             unsigned long long key[K::CAND];  // (|d|^2 as float bits) << 32 | slot
@@ -584,8 +595,13 @@ __device__ __forceinline__ void tri_vertex(WarpSmem<CT, TP>& S, int s) {
     typedef Cap<TP> K;
     uint32_t a, b, c;
     unpack<TP>(S.tid[s], a, b, c);
-    make_vertex<CT>(S.pnx[a], S.pny[a], S.pnz[a], S.ph[a], S.pnrm[a], S.pnx[b], S.pny[b], S.pnz[b], S.ph[b], S.pnrm[b],
-                    S.pnx[c], S.pny[c], S.pnz[c], S.ph[c], S.pnrm[c], S.tx[s], S.ty[s], S.tz[s], S.tev[s], S.trr[s]);
+    Vtx<CT> v;
+    CT rr;
+    const Pln<CT> A = S.pl[a], B = S.pl[b], C = S.pl[c];
+    make_vertex<CT>(A.x, A.y, A.z, A.h, S.pnrm[a], B.x, B.y, B.z, B.h, S.pnrm[b], C.x, C.y, C.z, C.h, S.pnrm[c], v.x, v.y,
+                    v.z, v.ev, rr);
+    S.tv[s] = v;
+    S.trr[s] = rr;
 }
 
 // Drop the planes that no vertex uses any more (their facets were cut away) and renumber the rest; the six
@@ -612,7 +628,8 @@ __device__ __noinline__ int compact_planes(WarpSmem<CT, TP>& S, const unsigned* 
         uint32_t qs = 0;
         uint8_t qc = 0;
         if (lv) {
-            qx = S.pnx[p]; qy = S.pny[p]; qz = S.pnz[p]; qh = S.ph[p]; qn = S.pnrm[p];
+            const Pln<CT> pq = S.pl[p];
+            qx = pq.x; qy = pq.y; qz = pq.z; qh = pq.h; qn = S.pnrm[p];
             qs = S.psrc[p]; qc = S.pcode[p];
         }
         unsigned m = __ballot_sync(0xffffffffu, lv);
@@ -620,7 +637,10 @@ __device__ __noinline__ int compact_planes(WarpSmem<CT, TP>& S, const unsigned* 
         base += __popc(m);
         __syncwarp();
         if (lv) {
-            S.pnx[q] = qx; S.pny[q] = qy; S.pnz[q] = qz; S.ph[q] = qh; S.pnrm[q] = qn;
+            Pln<CT> pq;
+            pq.x = qx; pq.y = qy; pq.z = qz; pq.h = qh;
+            S.pl[q] = pq;
+            S.pnrm[q] = qn;
             S.psrc[q] = qs; S.pcode[q] = qc;
             S.live[p] = (uint16_t)q;  // now the renumbering table
         }
@@ -641,8 +661,9 @@ __device__ __noinline__ int compact_planes(WarpSmem<CT, TP>& S, const unsigned* 
 // inside, 0 when the error bound does not decide.
 template <typename CT, int TP>
 __device__ __forceinline__ int side_fast(const WarpSmem<CT, TP>& S, int s, CT nx, CT ny, CT nz, CT h, CT nrm, CT hb) {
-    CT sv = f_fma<CT>(nx, S.tx[s], f_fma<CT>(ny, S.ty[s], f_fma<CT>(nz, S.tz[s], -h)));
-    CT bound = f_fma<CT>(nrm, S.tev[s], hb);
+    const Vtx<CT> v = S.tv[s];
+    CT sv = f_fma<CT>(nx, v.x, f_fma<CT>(ny, v.y, f_fma<CT>(nz, v.z, -h)));
+    CT bound = f_fma<CT>(nrm, v.ev, hb);
     if (sv > bound) return 1;
     if (sv < -bound) return -1;
     return 0;  // includes NaN / infinite bounds
@@ -736,7 +757,10 @@ __device__ int apply_cut(WarpSmem<CT, TP>& S, CellState<TP>& C, const unsigned* 
     }
     const int p = C.np++;
     if (lane == 0) {
-        S.pnx[p] = nx; S.pny[p] = ny; S.pnz[p] = nz; S.ph[p] = h; S.pnrm[p] = nrm;
+        Pln<CT> pq;
+        pq.x = nx; pq.y = ny; pq.z = nz; pq.h = h;
+        S.pl[p] = pq;
+        S.pnrm[p] = nrm;
         S.psrc[p] = src; S.pcode[p] = (uint8_t)code;
     }
     // boundary records, chunk by chunk (the lane's slot of chunk e is e * 32 + lane)
@@ -842,14 +866,15 @@ __device__ __forceinline__ void cell_box(const WarpSmem<CT, TP>& S, const CellSt
     for (int e = 0; e < TP; e++)
         if ((C.vm[e] >> lane) & 1u) {
             int s = e * 32 + lane;
-            CT ev = S.tev[s];
+            const Vtx<CT> v = S.tv[s];
+            CT ev = v.ev;
             if (!(ev < (CT)INFINITY)) inf = true;
-            lo0 = fminf(lo0, sub_dn(S.tx[s], ev));
-            lo1 = fminf(lo1, sub_dn(S.ty[s], ev));
-            lo2 = fminf(lo2, sub_dn(S.tz[s], ev));
-            hi0 = fmaxf(hi0, add_up(S.tx[s], ev));
-            hi1 = fmaxf(hi1, add_up(S.ty[s], ev));
-            hi2 = fmaxf(hi2, add_up(S.tz[s], ev));
+            lo0 = fminf(lo0, sub_dn(v.x, ev));
+            lo1 = fminf(lo1, sub_dn(v.y, ev));
+            lo2 = fminf(lo2, sub_dn(v.z, ev));
+            hi0 = fmaxf(hi0, add_up(v.x, ev));
+            hi1 = fmaxf(hi1, add_up(v.y, ev));
+            hi2 = fmaxf(hi2, add_up(v.z, ev));
         }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -1031,24 +1056,27 @@ __device__ int collect(WarpSmem<CT, TP>& S, const P* spos, int64_t N, const Geom
     return count;
 }
 
-// bitonic sort of the candidate keys [0..n) (padded to a power of two with +inf keys); equal distances
-// fall back to the collection slot, which is deterministic for a given input
+// Bitonic sort of the candidate keys [0, n) in increasing order, in the form whose compare-exchanges
+// all put the smaller key at the lower index (each merge starts by comparing every element of a block's lower half
+// with its mirror in the upper half).  Keys past n stand for +inf and are never touched: a comparison with one of
+// them at the higher index would leave both in place.  Keys are distinct (the collection slot is in the low bits).
 template <typename CT, int TP>
 __device__ void sort_cand(WarpSmem<CT, TP>& S, int n) {
     const unsigned lane = lane_id();
+    unsigned long long* key = S.u.cd.key;
     int m = 1;
     while (m < n) m <<= 1;
-    if (m < 2) return;
-    for (int k = n + (int)lane; k < m; k += 32) S.u.cd.key[k] = ~0ull;
-    __syncwarp();
+    const int half = m >> 1;
     for (int k = 2; k <= m; k <<= 1) {
         for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int i = (int)lane; i < m; i += 32) {
-                int ixj = i ^ jj;
-                if (ixj > i) {
-                    unsigned long long a = S.u.cd.key[i], b = S.u.cd.key[ixj];
-                    bool asc = (i & k) == 0;
-                    if ((a > b) == asc) { S.u.cd.key[i] = b; S.u.cd.key[ixj] = a; }
+            // the first stage of a merge pairs a with its mirror a ^ (k - 1), the later ones a with a + jj
+            const bool flip = jj == (k >> 1);
+            for (int i = (int)lane; i < half; i += 32) {
+                const int a = ((i & ~(jj - 1)) << 1) | (i & (jj - 1));
+                const int b = flip ? (a ^ (k - 1)) : (a + jj);
+                if (b < n) {
+                    unsigned long long x = key[a], y = key[b];
+                    if (x > y) { key[a] = y; key[b] = x; }
                 }
             }
             __syncwarp();
@@ -1089,19 +1117,24 @@ __device__ __forceinline__ void test_slots(const WarpSmem<CT, TP>& S, unsigned* 
     for (int e = 0; e < TP; e++) {
         unsigned m = pick<TP>(masks, e);
         if (!m) continue;
-        unsigned o = 0u;
+        unsigned o = 0u, um = 0u;
         do {
             const int l = __ffs(m) - 1;
             m &= m - 1;
-            const int s = e * 32 + l;
-            int sd = act ? side_fast<CT, TP>(S, s, nx, ny, nz, h, nrm, hb) : -1;
-            const bool und = act && sd == 0;
-            if (__any_sync(0xffffffffu, und)) {  // every lane calls: resolve may use warp collectives
-                const int r = resolve<P, CT, EXACT, TP>(S, s, und, src, code, spos, g, self, xws, cc, need_exact, ovf);
-                if (und) sd = r;
-            }
+            const int sd = act ? side_fast<CT, TP>(S, e * 32 + l, nx, ny, nz, h, nrm, hb) : -1;
             if (sd > 0) o |= 1u << l;
+            if (sd == 0) um |= 1u << l;
         } while (m);
+        // the tests the error bound left undecided, slot by slot (every lane calls: resolve may use warp
+        // collectives)
+        unsigned ua = __reduce_or_sync(0xffffffffu, um);
+        while (ua) {
+            const int l = __ffs(ua) - 1;
+            ua &= ua - 1;
+            const bool und = (um >> l) & 1u;
+            const int r = resolve<P, CT, EXACT, TP>(S, e * 32 + l, und, src, code, spos, g, self, xws, cc, need_exact, ovf);
+            if (und && r > 0) o |= 1u << l;
+        }
 #pragma unroll
         for (int q = 0; q < TP; q++)
             if (q == e) outm[q] |= o;
@@ -1206,7 +1239,10 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             nrm = (CT)1;
             code = CODE_WALL + (int)lane;
         }
-        S.pnx[lane] = nx; S.pny[lane] = ny; S.pnz[lane] = nz; S.ph[lane] = h; S.pnrm[lane] = nrm;
+        Pln<CT> pq;
+        pq.x = nx; pq.y = ny; pq.z = nz; pq.h = h;
+        S.pl[lane] = pq;
+        S.pnrm[lane] = nrm;
         S.psrc[lane] = src; S.pcode[lane] = (uint8_t)code;
     }
     __syncwarp();
@@ -1434,9 +1470,11 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         bool present = p < C.np && S.u.em.first[p] != 0xffffffffu;
         if (!present) continue;
         uint32_t t0 = S.u.em.first[p];
-        CT x0 = S.tx[t0], y0 = S.ty[t0], z0 = S.tz[t0];
+        const Vtx<CT> v0 = S.tv[t0];
+        CT x0 = v0.x, y0 = v0.y, z0 = v0.z;
         CT inrm = (CT)1 / S.pnrm[p];
-        CT nhx = S.pnx[p] * inrm, nhy = S.pny[p] * inrm, nhz = S.pnz[p] * inrm;
+        const Pln<CT> pp = S.pl[p];
+        CT nhx = pp.x * inrm, nhy = pp.y * inrm, nhz = pp.z * inrm;
         KSum<CT> kA;
         kA.zero();
         CT csx = 0, csy = 0, csz = 0, sm2 = 0;
@@ -1444,8 +1482,9 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         for (int guard = 0; guard < K::MAXT && cur != t0; guard++) {
             uint32_t nxt = succ_tri<CT, TP>(S, cur, p);
             if (nxt == t0) break;
-            CT x1 = S.tx[cur], y1 = S.ty[cur], z1 = S.tz[cur];
-            CT x2 = S.tx[nxt], y2 = S.ty[nxt], z2 = S.tz[nxt];
+            const Vtx<CT> v1 = S.tv[cur], v2 = S.tv[nxt];
+            CT x1 = v1.x, y1 = v1.y, z1 = v1.z;
+            CT x2 = v2.x, y2 = v2.y, z2 = v2.z;
             CT e1x = x1 - x0, e1y = y1 - y0, e1z = z1 - z0;
             CT e2x = x2 - x0, e2y = y2 - y0, e2z = z2 - z0;
             CT crx = f_fma<CT>(e1y, e2z, -e1z * e2y), cry = f_fma<CT>(e1z, e2x, -e1x * e2z),
@@ -1466,7 +1505,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         const CT A_ = kA.value();
         // distance from the site to the facet plane; tetrahedra (site, fan triangle) give
         // V_f = dist A_f / 3, first moment dist * sum(at (v0+v1+v2)/3) / 4, second moment dist/30 * sum(at s2)
-        CT dist = S.ph[p] * inrm;
+        CT dist = pp.h * inrm;
         kvol.add(dist * A_ * (CT)(1.0 / 3.0));
         mzx += dist * csx * (CT)0.25;
         mzy += dist * csy * (CT)0.25;
@@ -1501,7 +1540,8 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             if (fem[c]) {
                 int p = c * 32 + (int)lane;
                 Face f;
-                f.dx = (float)S.pnx[p]; f.dy = (float)S.pny[p]; f.dz = (float)S.pnz[p];
+                const Pln<CT> pf = S.pl[p];
+                f.dx = (float)pf.x; f.dy = (float)pf.y; f.dz = (float)pf.z;
                 f.area = (float)(sg * fA[c]);
                 f.cx = (float)fcx[c]; f.cy = (float)fcy[c]; f.cz = (float)fcz[c];
                 f.nbr = S.psrc[p];
@@ -1533,7 +1573,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
 // Exact kernel: Cap<16>, one warp per block, the listed cells, exact predicates.
 template <typename P, typename CT, bool EXACT, int TP, int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(32) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5;
     const unsigned lane = lane_id();
     WarpSmem<CT, TP>& S = reinterpret_cast<WarpSmem<CT, TP>*>(smem_raw)[w];
