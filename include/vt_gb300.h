@@ -73,8 +73,10 @@ typedef struct vt_params {
     int max_passes; /* candidate radius passes per cell before VT_ERR_SECURITY (default 1000) */
     int face_pool;  /* facet records reserved per particle (default 24; grown on demand) */
     int threads_per_cell; /* VT_FILTER32 only: 32 = one warp per cell (default; 0 means 32); 1 = one thread
-                             per cell first, 32 cells of a search-tree bucket per warp, the cells it cannot
-                             finish then taken by a warp each (same results) */
+                             per cell first, 32 cells of a search-tree bucket per warp; 4 or 8 = that many
+                             lanes per cell first (8 or 4 cells per warp, the cell in shared memory, the
+                             side tests split by vertex); in each case the cells the first kernel cannot
+                             finish are then taken by a warp each (same cells) */
     int reserved[3]; /* [0]: candidate pass sizing, 0 = radius doubling up to 2R, 1 = also limited (default)
                         by the density seen so far; others must be 0 */
 } vt_params;
@@ -199,7 +201,7 @@ int vt_probe_fp64_tflops(double *tflops, void *stream);
  *   boxes    host [n_sets][6]: lo x,y,z then hi x,y,z of each set's box; the
  *            cells of a set are clipped by its box walls (no periodic images)
  *   set_k    host [n_sets] k_target of each set, or NULL (p's k_target)
- *   set_tpc  host [n_sets] threads_per_cell of each set (1 or 32; 0 means 32),
+ *   set_tpc  host [n_sets] threads_per_cell of each set (1, 4, 8 or 32; 0 means 32),
  *            or NULL (p's threads_per_cell); see vt_autotune_batched
  *   p, stream  as for vt_build
  * A particle's neighbours are particles of its own set only.  The handle
@@ -219,7 +221,7 @@ int vt_build_batched(vt_handle *h, const void *pos, int dtype, const void *mass,
  * sets spread evenly through it, about `sample` points in all (<= 0: 262144),
  * are copied to a temporary device buffer and built as one batch for every
  * k_target in {16, 24, 32, 48, 64} and (FP32 filter) threads_per_cell in
- * {32, 1}; the configuration with the shortest clipping time (CUDA events)
+ * {32, 1, 4, 8}; the configuration with the shortest clipping time (CUDA events)
  * wins for every set of the class.
  *   pos, dtype, set_off, n_sets, boxes, p, stream  as for vt_build_batched
  *   k_out, tpc_out  host out [n_sets]: the chosen k_target and

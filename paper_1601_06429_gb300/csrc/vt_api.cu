@@ -142,6 +142,11 @@ void free_handle(vt_handle h) {
     delete h;
 }
 
+// threads per cell -> the clipping kernels' mode (ClipArgs): 32 -> 0, 1 -> 1, 4 -> 2, 8 -> 3; -1 if unsupported
+int tpc_mode_of(int tpc) {
+    return tpc == 32 ? 0 : tpc == 1 ? 1 : tpc == 4 ? 2 : tpc == 8 ? 3 : -1;
+}
+
 int cuda_rc(cudaError_t e) {
     if (e == cudaSuccess) return VT_OK;
     cudaGetLastError();
@@ -205,10 +210,13 @@ ClipArgs clip_args(vt_handle h) {
     a.sset = h->sset;
     a.sgeo = h->sgeo;
     a.soff = h->soff;
-    const bool thread_first = h->set_cfg ? h->any_thread != 0 : h->prm.threads_per_cell == 1;
+    // another kernel first (thread per cell, or a lane group) when some cell takes a mode other than the warp's
+    const bool thread_first = (h->modes & ~1) != 0;
     a.list_given = h->n_owned < h->N;
     a.warp_list = (thread_first || a.list_given) ? h->warp_list : nullptr;
     a.set_cfg = h->set_cfg;
+    a.tpc_mode = h->prm.precision == VT_FILTER32 ? tpc_mode_of(h->prm.threads_per_cell) : 0;
+    a.modes = h->modes;
     a.rad = h->rad;
     return a;
 }
@@ -293,7 +301,7 @@ int check_params(const vt_params* p, vt_params& prm) {
     if (prm.precision != VT_PLAIN64 && prm.precision != VT_FILTER32) return VT_ERR_INVALID;
     if (prm.reserved[0] < 0 || prm.reserved[0] > 1 || prm.reserved[1] || prm.reserved[2]) return VT_ERR_INVALID;
     if (prm.threads_per_cell == 0) prm.threads_per_cell = 32;
-    if (prm.threads_per_cell != 1 && prm.threads_per_cell != 32) return VT_ERR_INVALID;
+    if (tpc_mode_of(prm.threads_per_cell) < 0) return VT_ERR_INVALID;
     if (prm.k_target < 8 || prm.k_target > 120 || prm.max_passes < 1 || prm.max_passes > 100000 || prm.face_pool < 1 ||
         prm.face_pool > 128)
         return VT_ERR_INVALID;
@@ -401,11 +409,14 @@ int build_impl(vt_handle* out, const void* pos, int dtype, const void* mass, int
         h->set_in = A.get<uint32_t>(N);
         h->sgeo = A.get<Geometry>(n_sets);
         h->soff = A.get<int64_t>(n_sets + 1);
-        if (cfg_host) {
-            h->set_cfg = A.get<int32_t>(n_sets);
-            for (int k = 0; k < n_sets; k++)
-                if ((cfg_host[k] >> 16) & 1) h->any_thread = 1;
-        }
+        if (cfg_host) h->set_cfg = A.get<int32_t>(n_sets);
+    }
+    // the threads-per-cell modes present: each set's, or the handle's
+    if (cfg_host) {
+        for (int k = 0; k < n_sets; k++)
+            if (set_off[k + 1] > set_off[k]) h->modes |= 1 << ((cfg_host[k] >> 16) & 3);
+    } else {
+        h->modes = 1 << (prm.precision == VT_FILTER32 ? tpc_mode_of(prm.threads_per_cell) : 0);
     }
     for (int k = 0; k < 4; k++)
         if (cudaEventCreate(&h->ev[k]) != cudaSuccess) {
@@ -487,7 +498,7 @@ int vt_build_owned(vt_handle* out, const void* pos, int dtype, const void* mass,
     vt_params prm;
     int rc = check_params(p, prm);
     if (rc) return rc;
-    if (prm.threads_per_cell == 1) prm.threads_per_cell = 32;  // the listed cells go to the warp kernel
+    prm.threads_per_cell = 32;  // the listed cells go to the warp kernel
     Geometry geo;
     rc = make_geometry(box_lo, box_hi, periodic, prm.precision, geo);
     if (rc) return rc;
@@ -520,9 +531,9 @@ int vt_build_batched(vt_handle* out, const void* pos, int dtype, const void* mas
     for (int k = 0; cfg && k < n_sets && !rc; k++) {
         const int kt = set_k ? set_k[k] : prm.k_target;
         const int tpc = set_tpc ? (set_tpc[k] ? set_tpc[k] : 32) : prm.threads_per_cell;
-        if (kt < 8 || kt > 120 || (tpc != 1 && tpc != 32)) rc = VT_ERR_INVALID;
-        // the thread-per-cell kernel exists for the FP32 filter only
-        cfg[k] = kt | ((tpc == 1 && prm.precision == VT_FILTER32) ? (1 << 16) : 0);
+        if (kt < 8 || kt > 120 || tpc_mode_of(tpc) < 0) rc = VT_ERR_INVALID;
+        // the thread-per-cell and lane-group kernels exist for the FP32 filter only
+        cfg[k] = kt | (prm.precision == VT_FILTER32 && tpc_mode_of(tpc) > 0 ? tpc_mode_of(tpc) << 16 : 0);
     }
     if (!rc) rc = build_impl(out, pos, dtype, mass, N, sg[0], n_sets, set_off, sg, cfg, prm, stream);
     delete[] sg;
@@ -544,8 +555,8 @@ int vt_autotune_batched(const void* pos, int dtype, const int64_t* set_off, int 
     if (sample <= 0) sample = 262144;
     if (sample < 1024) sample = 1024;
     static const int ks[5] = {16, 24, 32, 48, 64};
-    const int tpcs[2] = {32, 1};
-    const int n_tpc = prm.precision == VT_FILTER32 ? 2 : 1;
+    const int tpcs[4] = {32, 1, 4, 8};
+    const int n_tpc = prm.precision == VT_FILTER32 ? 4 : 1;
     const size_t row = (dtype == VT_F32 ? sizeof(float) : sizeof(double)) * 3;
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < n_sets; k++) {

@@ -17,7 +17,10 @@ int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaS
     if (a.list_given) {
         // the cells to compute are listed: the warp kernel takes exactly those
     } else if (precision == VT_FILTER32 && a.warp_list) {
-        n += launch_clip_thread(a, dtype, sm_count, s);
+        // the thread-per-cell kernel also lists the cells of the warp mode, so it runs whenever either is present
+        if (a.modes & 3) n += launch_clip_thread(a, dtype, sm_count, s);
+        if (a.modes & 4) n += launch_clip_group(a, dtype, 4, sm_count, s);
+        if (a.modes & 8) n += launch_clip_group(a, dtype, 8, sm_count, s);
     } else {
         b.warp_list = nullptr;
     }

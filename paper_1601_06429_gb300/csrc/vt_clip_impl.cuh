@@ -797,42 +797,45 @@ __device__ int apply_cut(WarpSmem<CT, TP>& S, CellState<TP>& C, const unsigned* 
     __syncwarp();
     if (nB > K::MAXT) return CAP_BOUNDARY;
     // the new triangles take the nB lowest free slots: masks per chunk (warp-uniform)
-    int before[TP];
     int placed = 0;
 #pragma unroll
     for (int e = 0; e < TP; e++) {
         const unsigned fm = ~C.vm[e];
-        before[e] = placed;
         const unsigned nm = lowest_set_bits(fm, nB - placed);
         newm[e] = nm;
         placed += __popc(fm);
     }
     if (placed < nB) return CAP_TRIS;
-    // boundary rank r -> its slot; link tables by plane id
+    // the k-th lowest new slot takes boundary record k (its rank among the new slots, counted chunk by chunk);
+    // first the link tables by plane id, then the triangles
 #pragma unroll 1
-    for (int r = (int)lane; r < nB; r += 32) {
-        int e = 0;
-#pragma unroll
-        for (int q = 1; q < TP; q++)
-            if (r >= before[q]) e = q;
-        const uint32_t t = (uint32_t)(e * 32 + nth_set_bit(~pick<TP>(C.vm, e), r - before[e]));
-        const uint32_t rec = S.bnd[r];
-        S.lnk_s[rec & K::IDM] = (uint16_t)t;
-        S.lnk_e[(rec >> K::IDB) & K::IDM] = (uint16_t)t;
+    for (int e = 0, acc = 0; e < TP && acc < nB; e++) {
+        const unsigned nm = pick<TP>(newm, e);
+        if ((nm >> lane) & 1u) {
+            const uint32_t rec = S.bnd[acc + __popc(nm & lt)];
+            const uint32_t t = (uint32_t)(e * 32) + lane;
+            S.lnk_s[rec & K::IDM] = (uint16_t)t;
+            S.lnk_e[(rec >> K::IDB) & K::IDM] = (uint16_t)t;
+        }
+        acc += __popc(nm);
     }
     __syncwarp();
 #pragma unroll 1
-    for (int r = (int)lane; r < nB; r += 32) {
-        const uint32_t rec = S.bnd[r];
-        const uint32_t x = rec & K::IDM, y = (rec >> K::IDB) & K::IDM;
-        const uint32_t n = (rec >> (2 * K::IDB)) & ((1u << K::SB) - 1u), kn = rec >> (2 * K::IDB + K::SB);
-        const uint32_t t = S.lnk_s[x];  // the new triangle whose boundary edge starts at x
-        S.tid[t] = pack<TP>(x, y, (uint32_t)p);
-        S.tadj[t] = adj_pack(n, S.lnk_s[y], S.lnk_e[x]);
-        // redirect the kept neighbour's pointer (fields of one word may be updated by two new triangles)
-        atomicAnd(&S.tadj[n], ~(1023u << (10 * kn)));
-        atomicOr(&S.tadj[n], t << (10 * kn));
-        tri_vertex<CT, TP>(S, t);
+    for (int e = 0, acc = 0; e < TP && acc < nB; e++) {
+        const unsigned nm = pick<TP>(newm, e);
+        if ((nm >> lane) & 1u) {
+            const uint32_t rec = S.bnd[acc + __popc(nm & lt)];
+            const uint32_t x = rec & K::IDM, y = (rec >> K::IDB) & K::IDM;
+            const uint32_t n = (rec >> (2 * K::IDB)) & ((1u << K::SB) - 1u), kn = rec >> (2 * K::IDB + K::SB);
+            const uint32_t t = (uint32_t)(e * 32) + lane;
+            S.tid[t] = pack<TP>(x, y, (uint32_t)p);
+            S.tadj[t] = adj_pack(n, S.lnk_s[y], S.lnk_e[x]);
+            // redirect the kept neighbour's pointer (fields of one word may be updated by two new triangles)
+            atomicAnd(&S.tadj[n], ~(1023u << (10 * kn)));
+            atomicOr(&S.tadj[n], t << (10 * kn));
+            tri_vertex<CT, TP>(S, t);
+        }
+        acc += __popc(nm);
     }
 #pragma unroll
     for (int e = 0; e < TP; e++) {

@@ -606,18 +606,22 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
         b = __shfl_sync(0xffffffffu, b, 0);
         if ((int64_t)b >= nbuckets) break;
         const int64_t self64 = (int64_t)b * 32 + lane;
-        const bool alive = self64 < A.N;
+        bool alive = self64 < A.N;
         const uint32_t self = alive ? (uint32_t)self64 : 0u;
         Geometry g = A.geo;
         int64_t slo = 0, shi = A.N;
-        bool mine = alive;  // the cell's set is configured for this kernel
+        int mode = A.tpc_mode;
         if (A.sset && alive) {
             const uint32_t s = A.sset[self];
             g = A.sgeo[s];
             slo = A.soff[s];
             shi = A.soff[s + 1];
-            if (A.set_cfg) mine = ((A.set_cfg[s] >> 16) & 1) != 0;
+            if (A.set_cfg) mode = (A.set_cfg[s] >> 16) & 3;
         }
+        // this kernel's cells (mode 1); those of the warp kernel (mode 0) are handed over as they are, and those
+        // of the lane-group kernels (modes 2, 3) are left to them
+        if (mode >= 2) alive = false;
+        const bool mine = alive && mode == 1;
         if (!__any_sync(0xffffffffu, mine)) {
             // a bucket of warp-kernel sets: hand its cells over as they are
             const unsigned hm = __ballot_sync(0xffffffffu, alive);
@@ -853,6 +857,418 @@ __global__ void __launch_bounds__(TWARPS * 32) k_clip_thread(ClipArgs A) {
         atomicAdd(&A.st->n_t_fp64, v[2]);
         atomicAdd(&A.st->n_t_collected, v[4]);
         atomicAdd(&A.st->n_bucket_passes, v[3]);
+        atomicAdd(&A.st->n_collected, v[4]);
+    }
+}
+
+// ------------------------------------------------------------------ G lanes per cell (G = 4 or 8)
+// The lane-group kernels: G lanes share one cell and a warp holds 32/G cells (consecutive particles in Morton
+// order, a part of one tree bucket).  The warp streams the points near its cells through shared memory as the
+// thread-per-cell kernel does.  Each cell lives in shared memory: its G lanes filter a chunk's points in turn,
+// split every candidate's side tests (and their FP64 re-tests) by vertex, and combine the results with group
+// reductions; the group's first lane applies the cuts and keeps the cell's bounds.  The predicates, cuts,
+// certificate and emitted records are those of the thread-per-cell kernel, and so are the failure codes of the
+// cells handed to the warp kernel.
+constexpr int GWARPS = 2;  // warps per block
+
+struct GCell {
+    TCell C;
+    uint8_t pend[TCH];  // the chunk's points that survive the filter, in chunk order
+};
+
+// lanes of the G-lane group holding this lane
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    return ((1u << G) - 1u) << (lane_id() & ~(unsigned)(G - 1));
+}
+
+// Filter the chunk for the group's cell (lanes take points in turn, survivors kept in chunk order), then test the
+// survivors one after the other: side tests split by vertex, the cut by the group's first lane.  active, the
+// result and every branch are uniform over the group.  Returns 0 or a failure code.
+template <typename P, int G>
+__device__ int clip_chunk_group(const TSmem& S, int cnt, GCell& GC, const P* spos, const Geometry& g, const P& pi,
+                                uint32_t self, int64_t slo, int64_t shi, bool active, float slack, TCount& tc) {
+    TCell& C = GC.C;
+    const float u = Prec<float>::u();
+    const unsigned gmask = group_mask<G>();
+    const unsigned glt = gmask & lanemask_lt();
+    const int r = (int)(lane_id() & (unsigned)(G - 1));
+    const int leader = __ffs(gmask) - 1;
+    if (!active) return 0;
+    int np = 0;
+    {
+        const float qx = (float)pi.x, qy = (float)pi.y, qz = (float)pi.z;
+        const float iLx = 1.f / g.Lf[0], iLy = 1.f / g.Lf[1], iLz = 1.f / g.Lf[2];
+        const float bext = fmaxf(fmaxf(fmaxf(-C.bmin[0], C.bmax[0]), fmaxf(-C.bmin[1], C.bmax[1])),
+                                 fmaxf(-C.bmin[2], C.bmax[2]));
+        const float rad = 2.f * sqrtf(C.R2);
+        const float rskip = rad * (1.f + 1e-5f) + 4.f * slack;
+        const float rskip2 = rskip * rskip;
+        const float stol = 1e-5f * (4.f * bext * rad + rad * rad) + 8.f * slack * (bext + rad) + 1e-30f;
+        for (int k0 = 0; k0 < cnt; k0 += G) {
+            const int k = k0 + r;
+            bool keep = false;
+            uint32_t e = 0u;
+            if (k < cnt) {
+                e = S.key[k] & 255u;
+                const float4 q = S.chunk[e];
+                const uint32_t j = __float_as_uint(q.w);
+                float dx = q.x - qx, dy = q.y - qy, dz = q.z - qz;
+                if (g.periodic) {
+                    dx -= g.Lf[0] * rintf(dx * iLx);
+                    dy -= g.Lf[1] * rintf(dy * iLy);
+                    dz -= g.Lf[2] * rintf(dz * iLz);
+                }
+                const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+                keep = d2 <= rskip2 && j != self && (int64_t)j >= slo && (int64_t)j < shi;
+                if (keep) {
+                    const float sg = supp_g(dx, C.bmin[0], C.bmax[0]) + supp_g(dy, C.bmin[1], C.bmax[1]) +
+                                     supp_g(dz, C.bmin[2], C.bmax[2]);
+                    keep = !(sg < -stol);
+                }
+            }
+            const unsigned km = __ballot_sync(gmask, keep);
+            if (keep) GC.pend[np + __popc(km & glt)] = (uint8_t)e;
+            np += __popc(km);
+        }
+        __syncwarp(gmask);
+    }
+    for (int k = 0; k < np; k++) {
+        const float4 q = S.chunk[GC.pend[k]];
+        const uint32_t j = __float_as_uint(q.w);
+        float dx, dy, dz;
+        int code;
+        DispF<P, float>::get(spos[j], pi, g, dx, dy, dz, code);
+        const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+        if (d2 == 0.f) return TF_DUP;
+        if (d2 * (1.f - 8.f * u) > 4.f * C.R2) continue;
+        {
+            // the cell's box has shrunk since the filter
+            const float bext = fmaxf(fmaxf(fmaxf(-C.bmin[0], C.bmax[0]), fmaxf(-C.bmin[1], C.bmax[1])),
+                                     fmaxf(-C.bmin[2], C.bmax[2]));
+            const float rad2 = 4.f * C.R2;
+            const float stol = 1e-5f * (4.f * bext * sqrtf(rad2) + rad2) + 1e-30f;
+            const float sg = supp_g(dx, C.bmin[0], C.bmax[0]) + supp_g(dy, C.bmin[1], C.bmax[1]) +
+                             supp_g(dz, C.bmin[2], C.bmax[2]);
+            if (sg < -stol) continue;
+        }
+        const float h = 0.5f * d2;
+        const float nrm = sqrtf(d2);
+        const float hb = 16.f * u * h;
+        // the lane's vertices r, r + G, ...: beyond -> bm, undecided -> FP64 from the inputs
+        unsigned bm[TT / 32];
+#pragma unroll
+        for (int w = 0; w < TT / 32; w++) bm[w] = 0u;
+        int f = 0;
+        const int nT = C.nT;
+        for (int t = r; t < nT; t += G) {
+            const float4 v = C.V[t];
+            const float sv = __fmaf_rn(dx, v.x, __fmaf_rn(dy, v.y, __fmaf_rn(dz, v.z, -h)));
+            const float bound = __fmaf_rn(nrm, v.w, hb);
+            int sd = sv > bound ? 1 : (sv < -bound ? -1 : 0);
+            if (sd == 0 && !f) {
+                uint32_t a, b, c;
+                tri_ids(C.Tr[t], a, b, c);
+                const PRef ra = {C.Ps[a], C.Pc[a]}, rb = {C.Ps[b], C.Pc[b]}, rc = {C.Ps[c], C.Pc[c]};
+                const PRef rj = {j, (uint8_t)code};
+                sd = side64<P>(spos, g, self, ra, rb, rc, rj);
+                tc.fp64++;
+                if (sd == 0) f = TF_UNDECIDED;
+            }
+            if (sd > 0) bm[t >> 5] |= 1u << (t & 31);
+        }
+        if (r == 0) tc.tested++;
+        f = (int)__reduce_max_sync(gmask, (unsigned)f);
+        if (f) return f;
+        unsigned any = 0u;
+#pragma unroll
+        for (int w = 0; w < TT / 32; w++) {
+            bm[w] = __reduce_or_sync(gmask, bm[w]);
+            any |= bm[w];
+        }
+        if (!any) continue;
+        int cf = 0;
+        if (r == 0) {
+            cf = cut_cell(C, bm, dx, dy, dz, h, nrm, j, code);
+            if (!cf) {
+                tc.cut++;
+                bound_cell(C);
+            }
+        }
+        __syncwarp(gmask);
+        cf = __shfl_sync(gmask, cf, leader);
+        if (cf) return cf;
+    }
+    return 0;
+}
+
+template <typename P, int G>
+__global__ void __launch_bounds__(GWARPS * 32) k_clip_group(ClipArgs A) {
+    constexpr int W = 32 / G;            // cells per warp
+    constexpr int MODE = G == 4 ? 2 : 3;  // the threads-per-cell mode of this kernel's cells
+    extern __shared__ __align__(16) unsigned char gsmem[];
+    const int wib = (int)(threadIdx.x >> 5);
+    TSmem& S = reinterpret_cast<TSmem*>(gsmem)[wib];
+    const unsigned lane = lane_id(), lt = lanemask_lt();
+    const int gi = (int)(lane / G);       // the lane's cell within the warp
+    const int r = (int)(lane % G);        // its rank in the cell's group
+    const unsigned gmask = group_mask<G>();
+    GCell& GC = reinterpret_cast<GCell*>(gsmem + GWARPS * sizeof(TSmem))[wib * W + gi];
+    TCell& C = GC.C;
+    if (*((volatile unsigned*)&A.st->invalid_input)) return;
+    const P* spos = (const P*)A.spos;
+    const bool f64 = sizeof(P) != 16;
+    const float u = Prec<float>::u();
+    const int64_t nunits = (A.N + W - 1) / W;
+    TCount tc = {0ull, 0ull, 0ull, 0ull, 0ull};
+    for (;;) {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(&A.st->work_next_group[G == 4 ? 0 : 1], 1ull);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if ((int64_t)b >= nunits) break;
+        const int64_t self64 = (int64_t)b * W + gi;
+        bool alive = self64 < A.N;
+        const uint32_t self = alive ? (uint32_t)self64 : 0u;
+        Geometry g = A.geo;
+        int64_t slo = 0, shi = A.N;
+        int mode = A.tpc_mode;
+        if (A.sset && alive) {
+            const uint32_t s = A.sset[self];
+            g = A.sgeo[s];
+            slo = A.soff[s];
+            shi = A.soff[s + 1];
+            if (A.set_cfg) mode = (A.set_cfg[s] >> 16) & 3;
+        }
+        if (mode != MODE) alive = false;  // another kernel's cell
+        if (!__any_sync(0xffffffffu, alive)) continue;
+        const P pi = spos[self];
+        const float qx = (float)pi.x, qy = (float)pi.y, qz = (float)pi.z;
+        // the box of the warp's live cells and their index range
+        float blo[3] = {alive ? qx : INFINITY, alive ? qy : INFINITY, alive ? qz : INFINITY};
+        float bhi[3] = {alive ? qx : -INFINITY, alive ? qy : -INFINITY, alive ? qz : -INFINITY};
+        int64_t ilo = alive ? slo : INT64_MAX, ihi = alive ? shi : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                blo[a] = fminf(blo[a], __shfl_xor_sync(0xffffffffu, blo[a], o));
+                bhi[a] = fmaxf(bhi[a], __shfl_xor_sync(0xffffffffu, bhi[a], o));
+            }
+            ilo = min(ilo, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)ilo, o));
+            ihi = max(ihi, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)ihi, o));
+        }
+        // each cell's distance to its 4th nearest mate in its tree bucket (32 consecutive particles): lane l
+        // takes mate l, the warp sorts the distances once per cell
+        float near2 = INFINITY;
+        {
+            const int64_t jm = ((int64_t)b * W / 32) * 32 + lane;
+            float mx = 0.f, my = 0.f, mz = 0.f;
+            const bool mv = jm < A.N;
+            if (mv) {
+                const P pm = spos[jm];
+                mx = (float)pm.x; my = (float)pm.y; mz = (float)pm.z;
+            }
+            const bool per = A.sset == nullptr && A.geo.periodic;
+            for (int w = 0; w < W; w++) {
+                const float sx = __shfl_sync(0xffffffffu, qx, w * G), sy = __shfl_sync(0xffffffffu, qy, w * G),
+                            sz = __shfl_sync(0xffffffffu, qz, w * G);
+                const long long wlo = __shfl_sync(0xffffffffu, (long long)slo, w * G),
+                                whi = __shfl_sync(0xffffffffu, (long long)shi, w * G);
+                const int64_t sw = (int64_t)b * W + w;
+                float d2 = INFINITY;
+                if (mv && jm != sw && jm >= wlo && jm < whi) {
+                    float dx = fabsf(mx - sx), dy = fabsf(my - sy), dz = fabsf(mz - sz);
+                    if (per) {
+                        dx = fminf(dx, A.geo.Lf[0] - dx); dy = fminf(dy, A.geo.Lf[1] - dy); dz = fminf(dz, A.geo.Lf[2] - dz);
+                    }
+                    d2 = dx * dx + dy * dy + dz * dz;
+                }
+                for (int k = 2; k <= 32; k <<= 1)
+                    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                        const float o = __shfl_xor_sync(0xffffffffu, d2, jj);
+                        const bool up = ((lane & k) == 0), lower = (lane & jj) == 0;
+                        const float mn = fminf(d2, o), mx2 = fmaxf(d2, o);
+                        d2 = (lower == up) ? mn : mx2;
+                    }
+                const float d4w = __shfl_sync(0xffffffffu, d2, 3);
+                if (gi == w) near2 = d4w;
+            }
+        }
+        // the warp's first radius: 1.6 x the median over its live cells of that distance
+        float rho;
+        {
+            float d4 = alive ? near2 : INFINITY;
+            for (int k = 2; k <= 32; k <<= 1)
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    const float o = __shfl_xor_sync(0xffffffffu, d4, jj);
+                    const bool up = ((lane & k) == 0), lower = (lane & jj) == 0;
+                    const float mn = fminf(d4, o), mx = fmaxf(d4, o);
+                    d4 = (lower == up) ? mn : mx;
+                }
+            const int n_alive = __popc(__ballot_sync(0xffffffffu, alive));
+            d4 = __shfl_sync(0xffffffffu, d4, n_alive / 2);
+            if (d4 < INFINITY && d4 > 0.f) rho = 1.6f * sqrtf(d4);
+            else rho = (float)(2.0 * cbrt(g.L[0] * g.L[1] * g.L[2] / (double)max((int64_t)1, shi - slo)));
+            rho = __shfl_sync(0xffffffffu, rho, 0);
+        }
+        const double lmin = fmin(g.L[0], fmin(g.L[1], g.L[2]));
+        const float rho_cap = g.periodic ? (float)(0.24 * lmin) : INFINITY;
+        if (rho > rho_cap) rho = rho_cap;
+        if (!(near2 < INFINITY) || near2 <= 0.f) near2 = rho * rho * (1.f / 16.f);
+        float slack = 16.f * u * fmaxf(fmaxf(fmaxf(fabsf(g.hif[0]), fabsf(g.lof[0])), fmaxf(fabsf(g.hif[1]), fabsf(g.lof[1]))),
+                                        fmaxf(fmaxf(fabsf(g.hif[2]), fabsf(g.lof[2])), fmaxf(g.Lf[0], fmaxf(g.Lf[1], g.Lf[2])))) + 1e-30f;
+        slack = warp_max<float>(alive ? slack : 0.f);
+        // start box on the scale of the cell's own neighbourhood, set up by the group's first lane
+        int fail = 0;
+        {
+            const float Bown = fminf(4.f * rho, 3.f * sqrtf(near2));
+            if (alive && r == 0) fail = init_cell<P>(C, g, pi, self, Bown);
+            __syncwarp();
+            fail = __shfl_sync(0xffffffffu, fail, (int)(lane & ~(unsigned)(G - 1)));
+        }
+        const unsigned long long f64_before = tc.fp64;
+        bool done = !alive;
+        float g2prev = -1.f;
+        int streamed = 0;
+        for (int pass = 0; pass < TPASSES; pass++) {
+            const bool want = alive && !done && !fail;
+            if (!__any_sync(0xffffffffu, want)) break;
+            if (lane == 0) tc.passes++;
+            const float gr = rho * (1.f + 4.f * u) + slack;
+            const float g2hi = gr * gr * (1.f + 4.f * u);
+            int sp = 0;
+            {
+                const Tree& t = A.tree;
+                const int top = t.levels;
+                const int64_t span = (int64_t)1 << (5 * top);
+                bool hit = false;
+                float gap2 = -1.f;
+                if ((int64_t)lane < t.count[top] && lane * span < ihi && (lane + 1) * span > ilo) {
+                    const float4 lo = t.lo[t.off[top] + lane], hi = t.hi[t.off[top] + lane];
+                    const float dx = iv_gap(lo.x, hi.x, blo[0], bhi[0], g.Lf[0], g.periodic);
+                    const float dy = iv_gap(lo.y, hi.y, blo[1], bhi[1], g.Lf[1], g.periodic);
+                    const float dz = iv_gap(lo.z, hi.z, blo[2], bhi[2], g.Lf[2], g.periodic);
+                    gap2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+                    hit = gap2 < g2hi * 1.0001f + 1e-30f;
+                }
+                if (!hit) gap2 = -1.f;
+                const int nh = __popc(__ballot_sync(0xffffffffu, hit));
+                uint32_t val = hit ? (((uint32_t)top << 27) | lane) : 0xffffffffu;
+                warp_sort_desc(gap2, val);
+                if ((int)lane < nh) S.stack[lane] = val;
+                sp = nh;
+                __syncwarp();
+            }
+            bool ovf = false;
+            while (sp > 0) {
+                const int cnt = walk(S, sp, 0, (const float4*)A.spos, A.spos, f64, A.tree, g, blo, bhi, g2prev, g2hi,
+                                     ilo, ihi, ovf);
+                streamed += cnt;
+                if (lane == 0) tc.collected += cnt;
+                if (ovf || streamed > TMAXPTS) { ovf = true; break; }
+                if (cnt == 0) continue;
+                {
+                    const float cx = 0.5f * (blo[0] + bhi[0]), cy = 0.5f * (blo[1] + bhi[1]), cz = 0.5f * (blo[2] + bhi[2]);
+                    for (int k = (int)lane; k < cnt; k += 32) {
+                        const float4 q = S.chunk[k];
+                        float dx = fabsf(q.x - cx), dy = fabsf(q.y - cy), dz = fabsf(q.z - cz);
+                        if (g.periodic) {
+                            dx = fminf(dx, g.Lf[0] - dx); dy = fminf(dy, g.Lf[1] - dy); dz = fminf(dz, g.Lf[2] - dz);
+                        }
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        S.key[k] = (__float_as_uint(d2) & ~255u) | (uint32_t)k;
+                    }
+                    __syncwarp();
+                    sort_keys(S, cnt);
+                }
+                const bool act = alive && !done && !fail;
+                const int f = clip_chunk_group<P, G>(S, cnt, GC, spos, g, pi, self, slo, shi, act, slack, tc);
+                if (act && f) fail = f;
+                __syncwarp();
+            }
+            if (ovf) {
+                if (alive && !done && !fail) fail = TF_RADIUS;
+                break;
+            }
+            g2prev = g2hi;
+            if (alive && !done && !fail && 4.f * C.R2 <= rho * rho * (1.f - 8.f * u)) done = true;
+            float need = (alive && !done && !fail) ? 2.f * sqrtf(C.R2) * 1.001f : 0.f;
+            need = warp_max<float>(need);
+            if (need == 0.f) break;
+            float nxt = fminf(fmaxf(need, 1.25f * rho), 2.f * rho);
+            if (rho >= rho_cap) break;
+            rho = fminf(nxt, rho_cap);
+        }
+        if (alive && !done && !fail) fail = TF_RADIUS;
+        // ---------------- emission by the group's first lane (any lane of the group may have re-tested in FP64)
+        const bool used64 = (__ballot_sync(0xffffffffu, tc.fp64 != f64_before) & gmask) != 0u;
+        const bool lead = alive && r == 0;
+        int nf = 0;
+        uint64_t present = 0ull;
+        if (lead && !fail) {
+            nf = count_faces(C, &present);
+            if (nf < 0) fail = TF_WALL;
+        }
+        if (!(lead && !fail)) nf = 0;
+        int incl = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long base = 0ull;
+        if (lane == 0 && total > 0) base = atomicAdd(&A.st->face_next, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const bool pool_ok = base + (unsigned long long)total <= A.face_cap;
+        if (!pool_ok) {
+            if (lane == 0) atomicCAS(&A.st->error, 0, RC_POOL);
+            if (lead && !fail) fail = TF_CAP;
+        } else if (lead && !fail) {
+            const uint32_t start = (uint32_t)(base + (unsigned long long)(incl - nf));
+            float vol, mzx, mzy, mzz, m2;
+            if (!emit_faces(C, present, A.faces + start, vol, mzx, mzy, mzz, m2)) {
+                fail = TF_CAP_PLANES;
+            } else {
+                CellOut co;
+                co.vol = (double)vol;
+                co.zx = mzx / vol;
+                co.zy = mzy / vol;
+                co.zz = mzz / vol;
+                co.mom2 = m2;
+                A.cell[self] = co;
+                A.face_start[self] = start;
+                A.face_count[self] = (uint16_t)nf;
+                A.cstat[self] = (uint8_t)(CS_DONE | (used64 ? CS_FP64 : 0));
+                if (A.rad) A.rad[self] = sqrtf(C.R2) * (1.f + 1e-6f);
+                atomicMax(&A.st->max_faces, (unsigned)nf);
+            }
+        }
+        const bool emit = lead && !fail;
+        const bool hand = lead && !emit;
+        if (hand) atomicAdd(&A.st->n_tfail[fail > 0 && fail < 8 ? fail : 0], 1ull);
+        const unsigned hm = __ballot_sync(0xffffffffu, hand);
+        if (hm) {
+            unsigned slot0 = 0;
+            if (lane == 0) slot0 = atomicAdd(&A.st->n_warp_cells, (unsigned)__popc(hm));
+            slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+            if (hand) A.warp_list[slot0 + __popc(hm & lt)] = self;
+        }
+        int nfe = emit ? nf : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nfe += __shfl_xor_sync(0xffffffffu, nfe, o);
+        if (lane == 0 && nfe > 0) atomicAdd(&A.st->n_faces, (unsigned long long)nfe);
+        __syncwarp();
+    }
+    unsigned long long v[5] = {tc.tested, tc.cut, tc.fp64, tc.passes, tc.collected};
+#pragma unroll
+    for (int k = 0; k < 5; k++)
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0) {
+        atomicAdd(&A.st->n_tested, v[0]);
+        atomicAdd(&A.st->n_cut, v[1]);
+        atomicAdd(&A.st->n_fp64, v[2]);
         atomicAdd(&A.st->n_collected, v[4]);
     }
 }
@@ -1230,6 +1646,24 @@ __global__ void k_grid_finish(const double* __restrict__ acc, int64_t n, double 
     if (v < n) out[v] = (T)(acc[v] * inv_vox);
 }
 
+
+template <typename P, int G>
+int launch_group_t(const ClipArgs& a, int sm_count, cudaStream_t s) {
+    constexpr int W = 32 / G;
+    const size_t smem = GWARPS * (sizeof(TSmem) + W * sizeof(GCell));
+    static int per_sm_dev[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int per_sm = (dev >= 0 && dev < 64) ? per_sm_dev[dev] : 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_clip_group<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip_group<P, G>, GWARPS * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        if (dev >= 0 && dev < 64) per_sm_dev[dev] = per_sm;
+    }
+    k_clip_group<P, G><<<sm_count * per_sm, GWARPS * 32, smem, s>>>(a);
+    return 1;
+}
 }  // namespace
 
 int launch_grid_volume(const void* spos, int dtype, int64_t N, const Geometry& g, const Face* faces,
@@ -1279,6 +1713,11 @@ int launch_cvt_weighted(const void* spos, int dtype, int64_t N, const Geometry& 
         k_cvt_weighted<dpt4, TCellBig, true><<<rb, 128, 0, s>>>(a);
     }
     return 2;
+}
+
+int launch_clip_group(const ClipArgs& a, int dtype, int lanes, int sm_count, cudaStream_t s) {
+    if (dtype == VT_F32) return lanes == 4 ? launch_group_t<float4, 4>(a, sm_count, s) : launch_group_t<float4, 8>(a, sm_count, s);
+    return lanes == 4 ? launch_group_t<dpt4, 4>(a, sm_count, s) : launch_group_t<dpt4, 8>(a, sm_count, s);
 }
 
 int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s) {

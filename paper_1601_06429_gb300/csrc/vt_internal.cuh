@@ -49,6 +49,7 @@ struct DevStatus {
     unsigned long long n_tfail[8];        // ... by reason (capacity, ill-conditioned vertex, undecided in FP64,
                                           // duplicate, start box too small, security radius not reached)
     unsigned long long n_t_tested, n_t_cut, n_t_fp64, n_t_collected;  // its own counters
+    unsigned long long work_next_group[2];  // unit schedulers of the four- and eight-lane kernels
 };
 
 // facet record (one per cell side of a facet between two particles)
@@ -99,7 +100,7 @@ struct vt_handle_s {
     vt::Geometry* sgeo; // [n_sets]
     int64_t* soff;      // [n_sets+1] index range of each set (input and sorted order alike)
     int32_t* set_cfg;   // [n_sets] per-set k_target | thread-per-cell flag << 16, or NULL
-    int any_thread;     // some set takes the thread-per-cell kernel
+    int modes;          // threads-per-cell modes present among the cells (bit m: mode m, see ClipArgs)
     // sorted particles
     void* spos;         // float4 (f32) or double4-like 4 doubles (f64): x,y,z,m
     uint32_t* perm;     // sorted -> input index

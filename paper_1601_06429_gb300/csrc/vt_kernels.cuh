@@ -54,12 +54,16 @@ struct ClipArgs {
     const uint32_t* sset;
     const Geometry* sgeo;
     const int64_t* soff;
-    // FP32 filter: the thread-per-cell kernel runs first and lists here (N entries) the cells the warp kernel
-    // must take; NULL: the warp kernel takes every cell
+    // FP32 filter: the thread-per-cell and lane-group kernels run first and list here (N entries) the cells the
+    // warp kernel must take; NULL: the warp kernel takes every cell
     uint32_t* warp_list;
-    // batched sets: per-set clipping configuration (k_target in the low 16 bits, bit 16: thread-per-cell
-    // kernel first), or NULL for the handle's parameters
+    // batched sets: per-set clipping configuration (k_target in the low 16 bits, bits 16-17: the threads-per-cell
+    // mode below), or NULL for the handle's parameters
     const int32_t* set_cfg;
+    // threads per cell as a mode: 0 one warp, 1 one thread, 2 four lanes, 3 eight lanes (the handle's; cells of
+    // sets with a configuration take that set's), and the modes present among the cells (bit m: mode m)
+    int tpc_mode;
+    int modes;
     // list_given: warp_list already holds the cells to compute (st->n_warp_cells of them; the other particles
     // are candidates only) and no thread-per-cell kernel runs
     int list_given;
@@ -69,6 +73,7 @@ struct ClipArgs {
 int launch_clip(const ClipArgs& a, int dtype, int precision, int sm_count, cudaStream_t s);
 int launch_clip_exact(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
 int launch_clip_thread(const ClipArgs& a, int dtype, int sm_count, cudaStream_t s);
+int launch_clip_group(const ClipArgs& a, int dtype, int lanes, int sm_count, cudaStream_t s);
 int launch_fma_probe(int blocks, int iters, float* sink, cudaStream_t s);
 int launch_fma_probe64(int blocks, int iters, double* sink, cudaStream_t s);
 int launch_cvt_weighted(const void* spos, int dtype, int64_t N, const Geometry& g, const Face* faces,

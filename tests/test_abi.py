@@ -130,7 +130,8 @@ def test_batched_rejects_bad_sets_without_device_work(lib):
     assert batched(good, 3, bx=flat) == binding.VT_ERR_INVALID
     assert batched(good, 3, set_k=I32(24, 7, 24)) == binding.VT_ERR_INVALID        # k_target below 8
     assert batched(good, 3, set_k=I32(24, 121, 24)) == binding.VT_ERR_INVALID      # k_target above 120
-    assert batched(good, 3, set_tpc=I32(32, 1, 4)) == binding.VT_ERR_INVALID       # only 1 or 32 threads per cell
+    assert batched(good, 3, set_tpc=I32(32, 1, 2)) == binding.VT_ERR_INVALID       # only 1, 4, 8 or 32 threads per cell
+    assert batched(good, 3, set_tpc=I32(16, 1, 4)) == binding.VT_ERR_INVALID
     p = binding.vt_default_params()
     p.threads_per_cell = 2
     assert batched(good, 3, p=p) == binding.VT_ERR_INVALID

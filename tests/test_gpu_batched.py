@@ -60,7 +60,8 @@ def sets64():
     return inputs.halo_sets(n_sets=64, nmin=64, nmax=4096, seed=6, dtype=np.float32)
 
 
-@pytest.mark.parametrize("precision,tol,tpc", [("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("plain64", 1e-6, 32)])
+@pytest.mark.parametrize("precision,tol,tpc", [("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("filter32", 2e-5, 4),
+                                               ("filter32", 2e-5, 8), ("plain64", 1e-6, 32)])
 def test_batched_matches_oracle_every_set(sets64, oracle_mod, precision, tol, tpc):
     pts, off = sets64
     boxes = unit_boxes(len(off) - 1)
@@ -124,7 +125,8 @@ def test_batched_varied_boxes_and_degenerate_sets(oracle_mod):
     pts = np.concatenate(parts)
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     boxes = np.array(boxes)
-    for precision, tol, tpc in (("plain64", 1e-6, 32), ("filter32", 2e-5, 32), ("filter32", 2e-5, 1)):
+    for precision, tol, tpc in (("plain64", 1e-6, 32), ("filter32", 2e-5, 32), ("filter32", 2e-5, 1),
+                                ("filter32", 2e-5, 4), ("filter32", 2e-5, 8)):
         h, vol, noff, ids = run_batched(pts, off, boxes, precision, tpc)
         for s in range(len(sizes)):
             check_set(s, off, boxes[s], vol, noff, ids, pts, oracle_mod, tol)
@@ -135,12 +137,12 @@ def test_batched_varied_boxes_and_degenerate_sets(oracle_mod):
 
 
 def test_per_set_configuration_matches_oracle(sets64, oracle_mod):
-    """Each set with its own k_target and kernel (thread- or warp-per-cell), mixed in one batch."""
+    """Each set with its own k_target and kernel (1, 4, 8 or 32 threads per cell), mixed in one batch."""
     pts, off = sets64
     n_sets = len(off) - 1
     g = np.random.default_rng(21)
     set_k = g.choice([16, 24, 32, 48, 64], n_sets).astype(np.int32)
-    set_tpc = g.choice([1, 32], n_sets).astype(np.int32)
+    set_tpc = g.choice([1, 4, 8, 32], n_sets).astype(np.int32)
     boxes = unit_boxes(n_sets)
     pos = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
     h = vt.vt_build_batched(pos, off, boxes, set_k=set_k, set_tpc=set_tpc)
@@ -156,7 +158,7 @@ def test_autotune_choices_are_valid_and_change_no_cell(sets64):
     boxes = unit_boxes(n_sets)
     pos = torch.from_numpy(np.ascontiguousarray(pts)).cuda()
     set_k, set_tpc = vt.vt_autotune_batched(pos, off, boxes, sample=16384)
-    assert set(set_k.tolist()) <= {16, 24, 32, 48, 64} and set(set_tpc.tolist()) <= {1, 32}
+    assert set(set_k.tolist()) <= {16, 24, 32, 48, 64} and set(set_tpc.tolist()) <= {1, 4, 8, 32}
     # sets of one size class share their choice
     cls = np.floor(np.log2(np.diff(off))).astype(int)
     for c in np.unique(cls):

@@ -100,10 +100,12 @@ def test_uniform4096_filter32(uniform4096, oracle_mod):
     assert abs(g["vol"].sum() - 1.0) < 1e-6
 
 
-def test_uniform4096_thread_per_cell(uniform4096, oracle_mod):
-    """The thread-per-cell clipping kernel (cells it cannot finish go to the warp kernel) against the oracle."""
+@pytest.mark.parametrize("tpc", [1, 4, 8])
+def test_uniform4096_thread_per_cell(uniform4096, oracle_mod, tpc):
+    """The thread-per-cell and lane-group clipping kernels (cells they cannot finish go to the warp kernel) against
+    the oracle."""
     x, o = uniform4096
-    g = gpu_run(x, 0.0, 1.0, True, "filter32", threads_per_cell=1)
+    g = gpu_run(x, 0.0, 1.0, True, "filter32", threads_per_cell=tpc)
     check_cells(g, o, oracle_mod, np.arange(len(x)), 2e-5)
     assert abs(g["vol"].sum() - 1.0) < 1e-6
     check_gradient(g, x, o, oracle_mod, np.arange(len(x)), 0.0, 1.0, 1e-3, 1e-4)
@@ -167,7 +169,8 @@ def clustered64k(oracle_mod):
     return x, L, oracle_mod.cells(x.astype(np.float64), 0.0, L, True, mode="certified")
 
 
-@pytest.mark.parametrize("prec,tol,tpc", [("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("plain64", 1e-6, 32)])
+@pytest.mark.parametrize("prec,tol,tpc", [("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("filter32", 2e-5, 4),
+                                          ("filter32", 2e-5, 8), ("plain64", 1e-6, 32)])
 def test_clustered64k_all_cells(clustered64k, oracle_mod, prec, tol, tpc):
     x, L, o = clustered64k
     g = gpu_run(x, 0.0, L, True, prec, threads_per_cell=tpc)
@@ -241,7 +244,8 @@ def test_bounded_halo_sets(oracle_mod):
     for s in range(3):
         x = pts[off[s]:off[s + 1]]
         o = oracle_mod.cells(x.astype(np.float64), -1.0, 1.0, False, mode="certified")
-        for prec, tol, tpc in (("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("plain64", 1e-6, 32)):
+        for prec, tol, tpc in (("filter32", 2e-5, 32), ("filter32", 2e-5, 1), ("filter32", 2e-5, 4),
+                               ("filter32", 2e-5, 8), ("plain64", 1e-6, 32)):
             g = gpu_run(x, -1.0, 1.0, False, prec, threads_per_cell=tpc)
             check_cells(g, o, oracle_mod, np.arange(len(x)), tol)
             assert abs(g["vol"].sum() - 8.0) < 8e-6
