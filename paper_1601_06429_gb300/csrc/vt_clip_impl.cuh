@@ -1074,13 +1074,19 @@ __device__ void sort_cand(WarpSmem<CT, TP>& S, int n) {
         for (int jj = k >> 1; jj > 0; jj >>= 1) {
             // the first stage of a merge pairs a with its mirror a ^ (k - 1), the later ones a with a + jj
             const bool flip = jj == (k >> 1);
-            for (int i = (int)lane; i < half; i += 32) {
-                const int a = ((i & ~(jj - 1)) << 1) | (i & (jj - 1));
-                const int b = flip ? (a ^ (k - 1)) : (a + jj);
-                if (b < n) {
-                    unsigned long long x = key[a], y = key[b];
-                    if (x > y) { key[a] = y; key[b] = x; }
-                }
+            for (int i = (int)lane; i < half; i += 64) {
+                // pairs i and i + 32 (disjoint: every index is in one pair of a stage)
+                const int i1 = i + 32;
+                const int a0 = ((i & ~(jj - 1)) << 1) | (i & (jj - 1));
+                const int b0 = flip ? (a0 ^ (k - 1)) : (a0 + jj);
+                const int a1 = ((i1 & ~(jj - 1)) << 1) | (i1 & (jj - 1));
+                const int b1 = flip ? (a1 ^ (k - 1)) : (a1 + jj);
+                const bool v0 = b0 < n, v1 = i1 < half && b1 < n;
+                unsigned long long x0 = 0ull, y0 = 0ull, x1 = 0ull, y1 = 0ull;
+                if (v0) { x0 = key[a0]; y0 = key[b0]; }
+                if (v1) { x1 = key[a1]; y1 = key[b1]; }
+                if (v0 && x0 > y0) { key[a0] = y0; key[b0] = x0; }
+                if (v1 && x1 > y1) { key[a1] = y1; key[b1] = x1; }
             }
             __syncwarp();
         }
@@ -1122,11 +1128,15 @@ __device__ __forceinline__ void test_slots(const WarpSmem<CT, TP>& S, unsigned* 
         if (!m) continue;
         unsigned o = 0u, um = 0u;
         do {
-            const int l = __ffs(m) - 1;
+            // two slots per iteration (the second repeats the first when one is left: the same result)
+            const int l0 = __ffs(m) - 1;
             m &= m - 1;
-            const int sd = act ? side_fast<CT, TP>(S, e * 32 + l, nx, ny, nz, h, nrm, hb) : -1;
-            if (sd > 0) o |= 1u << l;
-            if (sd == 0) um |= 1u << l;
+            const int l1 = m ? __ffs(m) - 1 : l0;
+            m &= m - 1;
+            const int sd0 = act ? side_fast<CT, TP>(S, e * 32 + l0, nx, ny, nz, h, nrm, hb) : -1;
+            const int sd1 = act ? side_fast<CT, TP>(S, e * 32 + l1, nx, ny, nz, h, nrm, hb) : -1;
+            o |= (sd0 > 0 ? 1u << l0 : 0u) | (sd1 > 0 ? 1u << l1 : 0u);
+            um |= (sd0 == 0 ? 1u << l0 : 0u) | (sd1 == 0 ? 1u << l1 : 0u);
         } while (m);
         // the tests the error bound left undecided, slot by slot (every lane calls: resolve may use warp
         // collectives)
