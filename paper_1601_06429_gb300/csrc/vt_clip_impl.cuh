@@ -846,31 +846,22 @@ __device__ int apply_cut(WarpSmem<CT, TP>& S, CellState<TP>& C, const unsigned* 
     return 0;
 }
 
+// One pass over the vertices: the bound of |v|^2 (returned; the security radius is twice its root) and the box
+// around the exact vertices (positions widened by their error bounds), as floats rounded outward
 template <typename CT, int TP>
-__device__ __forceinline__ CT rmax2(const WarpSmem<CT, TP>& S, const CellState<TP>& C) {
+__device__ __forceinline__ CT radius_box(const WarpSmem<CT, TP>& S, const CellState<TP>& C, float* bmin, float* bmax) {
+    const unsigned lane = lane_id();
     CT r = 0;
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int e = 0; e < TP; e++)
-        if ((C.vm[e] >> lane) & 1u) {
-            CT v = S.trr[e * 32 + lane];
-            r = r > v ? r : v;
-        }
-    return warp_max<CT>(r);
-}
-
-// Box around the exact vertices (positions widened by their error bounds), as floats rounded outward.
-template <typename CT, int TP>
-__device__ __forceinline__ void cell_box(const WarpSmem<CT, TP>& S, const CellState<TP>& C, float* bmin, float* bmax) {
-    const unsigned lane = lane_id();
     float lo0 = 0.f, lo1 = 0.f, lo2 = 0.f, hi0 = 0.f, hi1 = 0.f, hi2 = 0.f;  // the site is inside
     bool inf = false;
 #pragma unroll
     for (int e = 0; e < TP; e++)
         if ((C.vm[e] >> lane) & 1u) {
-            int s = e * 32 + lane;
+            const int s = e * 32 + lane;
+            const CT rr = S.trr[s];
+            r = r > rr ? r : rr;
             const Vtx<CT> v = S.tv[s];
-            CT ev = v.ev;
+            const CT ev = v.ev;
             if (!(ev < (CT)INFINITY)) inf = true;
             lo0 = fminf(lo0, sub_dn(v.x, ev));
             lo1 = fminf(lo1, sub_dn(v.y, ev));
@@ -881,6 +872,8 @@ __device__ __forceinline__ void cell_box(const WarpSmem<CT, TP>& S, const CellSt
         }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
+        const CT ro = __shfl_xor_sync(0xffffffffu, r, o);
+        r = r > ro ? r : ro;
         lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
         lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
         lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
@@ -894,6 +887,7 @@ __device__ __forceinline__ void cell_box(const WarpSmem<CT, TP>& S, const CellSt
     }
     bmin[0] = lo0; bmin[1] = lo1; bmin[2] = lo2;
     bmax[0] = hi0; bmax[1] = hi1; bmax[2] = hi2;
+    return r;
 }
 
 // ------------------------------------------------------------------ tree search
@@ -1281,9 +1275,8 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
     C.vm[0] = 0xFFu;
     C.hw = 8;
     __syncwarp();
-    CT R2 = rmax2<CT, TP>(S, C);
     float bmin[3], bmax[3];
-    cell_box<CT, TP>(S, C, bmin, bmax);
+    CT R2 = radius_box<CT, TP>(S, C, bmin, bmax);
 
     CT rlo2 = 0;
     const double lmin = fmin(g.L[0], fmin(g.L[1], g.L[2]));
@@ -1405,8 +1398,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
             }
             if (any_cut) {
                 VT_T0(tb0);
-                R2 = rmax2<CT, TP>(S, C);
-                cell_box<CT, TP>(S, C, bmin, bmax);
+                R2 = radius_box<CT, TP>(S, C, bmin, bmax);
                 VT_T1(cc, 8, tb0);
             }
             VT_T1(cc, 3, tk0);
@@ -1466,78 +1458,16 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
         if (__any_sync(0xffffffffu, art)) return RC_RETRY_BOX;
         if (g.periodic && __any_sync(0xffffffffu, on)) return VT_ERR_UNSUPPORTED;
     }
-    // facets: lane (chunk c) walks plane c*32+lane; fan from the facet's first vertex
+    // facets: lane (chunk c) walks plane c*32+lane; fan from the facet's first vertex.  The facet records are
+    // reserved first (a facet is a plane present that is a bisector) and written as their sums come out.
     constexpr int PCH = K::MAXP / 32;
-    // the volume (and each facet area) is summed with compensation; the moments plainly
-    KSum<CT> kvol;
-    kvol.zero();
-    CT mzx = 0, mzy = 0, mzz = 0, m2 = 0;
-    CT fA[PCH], fcx[PCH], fcy[PCH], fcz[PCH];
-    bool fem[PCH];
-#pragma unroll 1
-    for (int c = 0; c < PCH; c++) {
-        fem[c] = false;
-        fA[c] = fcx[c] = fcy[c] = fcz[c] = (CT)0;
-        if (c * 32 >= C.np) continue;
-        int p = c * 32 + (int)lane;
-        bool present = p < C.np && S.u.em.first[p] != 0xffffffffu;
-        if (!present) continue;
-        uint32_t t0 = S.u.em.first[p];
-        const Vtx<CT> v0 = S.tv[t0];
-        CT x0 = v0.x, y0 = v0.y, z0 = v0.z;
-        CT inrm = (CT)1 / S.pnrm[p];
-        const Pln<CT> pp = S.pl[p];
-        CT nhx = pp.x * inrm, nhy = pp.y * inrm, nhz = pp.z * inrm;
-        KSum<CT> kA;
-        kA.zero();
-        CT csx = 0, csy = 0, csz = 0, sm2 = 0;
-        uint32_t cur = succ_tri<CT, TP>(S, t0, p);
-        for (int guard = 0; guard < K::MAXT && cur != t0; guard++) {
-            uint32_t nxt = succ_tri<CT, TP>(S, cur, p);
-            if (nxt == t0) break;
-            const Vtx<CT> v1 = S.tv[cur], v2 = S.tv[nxt];
-            CT x1 = v1.x, y1 = v1.y, z1 = v1.z;
-            CT x2 = v2.x, y2 = v2.y, z2 = v2.z;
-            CT e1x = x1 - x0, e1y = y1 - y0, e1z = z1 - z0;
-            CT e2x = x2 - x0, e2y = y2 - y0, e2z = z2 - z0;
-            CT crx = f_fma<CT>(e1y, e2z, -e1z * e2y), cry = f_fma<CT>(e1z, e2x, -e1x * e2z),
-               crz = f_fma<CT>(e1x, e2y, -e1y * e2x);
-            CT at = (CT)0.5 * f_fma<CT>(crx, nhx, f_fma<CT>(cry, nhy, crz * nhz));
-            kA.add(at);
-            CT third = (CT)(1.0 / 3.0);
-            csx = f_fma<CT>(at * third, x0 + x1 + x2, csx);
-            csy = f_fma<CT>(at * third, y0 + y1 + y2, csy);
-            csz = f_fma<CT>(at * third, z0 + z1 + z2, csz);
-            // |y|^2 moment of the tetrahedron (site, v0, v1, v2) without its volume factor
-            CT s2 = f_fma<CT>(x0, x0 + x1 + x2, f_fma<CT>(y0, y0 + y1 + y2, z0 * (z0 + z1 + z2)));
-            s2 = f_fma<CT>(x1, x1 + x2, f_fma<CT>(y1, y1 + y2, f_fma<CT>(z1, z1 + z2, s2)));
-            s2 = f_fma<CT>(x2, x2, f_fma<CT>(y2, y2, f_fma<CT>(z2, z2, s2)));
-            sm2 = f_fma<CT>(at, s2, sm2);
-            cur = nxt;
-        }
-        const CT A_ = kA.value();
-        // distance from the site to the facet plane; tetrahedra (site, fan triangle) give
-        // V_f = dist A_f / 3, first moment dist * sum(at (v0+v1+v2)/3) / 4, second moment dist/30 * sum(at s2)
-        CT dist = pp.h * inrm;
-        kvol.add(dist * A_ * (CT)(1.0 / 3.0));
-        mzx += dist * csx * (CT)0.25;
-        mzy += dist * csy * (CT)0.25;
-        mzz += dist * csz * (CT)0.25;
-        m2 += dist * sm2 * (CT)(1.0 / 30.0);
-        if (A_ != (CT)0) { fcx[c] = csx / A_; fcy[c] = csy / A_; fcz[c] = csz / A_; }
-        fA[c] = A_;
-        fem[c] = (p >= 6) && S.pcode[p] < 27;
-    }
-    kvol.warp_reduce();
-    CT vol = kvol.value();
-    m2 = warp_sum<CT>(m2);
-    mzx = warp_sum<CT>(mzx); mzy = warp_sum<CT>(mzy); mzz = warp_sum<CT>(mzz);
-    const CT sg = vol < 0 ? (CT)-1 : (CT)1;
-    vol *= sg; m2 *= sg;
     int nf_total = 0;
 #pragma unroll
-    for (int c = 0; c < PCH; c++) nf_total += __popc(__ballot_sync(0xffffffffu, fem[c]));
-    // reserve facet records
+    for (int c = 0; c < PCH; c++) {
+        const int p = c * 32 + (int)lane;
+        const bool f = p < C.np && p >= 6 && S.pcode[p] < 27 && S.u.em.first[p] != 0xffffffffu;
+        nf_total += __popc(__ballot_sync(0xffffffffu, f));
+    }
     uint32_t start = 0;
     if (lane == 0 && nf_total > 0) {
         unsigned long long s0 = atomicAdd(&A.st->face_next, (unsigned long long)nf_total);
@@ -1545,23 +1475,82 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
     }
     start = __shfl_sync(0xffffffffu, start, 0);
     if (start == 0xffffffffu) return RC_POOL;
-    {
-        int acc = 0;
-#pragma unroll
-        for (int c = 0; c < PCH; c++) {
-            unsigned m = __ballot_sync(0xffffffffu, fem[c]);
-            if (fem[c]) {
-                int p = c * 32 + (int)lane;
-                Face f;
-                const Pln<CT> pf = S.pl[p];
-                f.dx = (float)pf.x; f.dy = (float)pf.y; f.dz = (float)pf.z;
-                f.area = (float)(sg * fA[c]);
-                f.cx = (float)fcx[c]; f.cy = (float)fcy[c]; f.cz = (float)fcz[c];
-                f.nbr = S.psrc[p];
-                A.faces[start + acc + __popc(m & lt)] = f;
+    // the volume (and each facet area) is summed with compensation; the moments plainly
+    KSum<CT> kvol;
+    kvol.zero();
+    CT mzx = 0, mzy = 0, mzz = 0, m2 = 0;
+    int acc = 0;
+#pragma unroll 1
+    for (int c = 0; c < PCH; c++) {
+        if (c * 32 >= C.np) break;
+        int p = c * 32 + (int)lane;
+        bool present = p < C.np && S.u.em.first[p] != 0xffffffffu;
+        const bool fem = present && (p >= 6) && S.pcode[p] < 27;
+        const unsigned fm = __ballot_sync(0xffffffffu, fem);
+        if (present) {
+            uint32_t t0 = S.u.em.first[p];
+            const Vtx<CT> v0 = S.tv[t0];
+            CT x0 = v0.x, y0 = v0.y, z0 = v0.z;
+            CT inrm = (CT)1 / S.pnrm[p];
+            const Pln<CT> pp = S.pl[p];
+            CT nhx = pp.x * inrm, nhy = pp.y * inrm, nhz = pp.z * inrm;
+            KSum<CT> kA;
+            kA.zero();
+            CT csx = 0, csy = 0, csz = 0, sm2 = 0;
+            uint32_t cur = succ_tri<CT, TP>(S, t0, p);
+            for (int guard = 0; guard < K::MAXT && cur != t0; guard++) {
+                uint32_t nxt = succ_tri<CT, TP>(S, cur, p);
+                if (nxt == t0) break;
+                const Vtx<CT> v1 = S.tv[cur], v2 = S.tv[nxt];
+                CT x1 = v1.x, y1 = v1.y, z1 = v1.z;
+                CT x2 = v2.x, y2 = v2.y, z2 = v2.z;
+                CT e1x = x1 - x0, e1y = y1 - y0, e1z = z1 - z0;
+                CT e2x = x2 - x0, e2y = y2 - y0, e2z = z2 - z0;
+                CT crx = f_fma<CT>(e1y, e2z, -e1z * e2y), cry = f_fma<CT>(e1z, e2x, -e1x * e2z),
+                   crz = f_fma<CT>(e1x, e2y, -e1y * e2x);
+                CT at = (CT)0.5 * f_fma<CT>(crx, nhx, f_fma<CT>(cry, nhy, crz * nhz));
+                kA.add(at);
+                CT third = (CT)(1.0 / 3.0);
+                csx = f_fma<CT>(at * third, x0 + x1 + x2, csx);
+                csy = f_fma<CT>(at * third, y0 + y1 + y2, csy);
+                csz = f_fma<CT>(at * third, z0 + z1 + z2, csz);
+                // |y|^2 moment of the tetrahedron (site, v0, v1, v2) without its volume factor
+                CT s2 = f_fma<CT>(x0, x0 + x1 + x2, f_fma<CT>(y0, y0 + y1 + y2, z0 * (z0 + z1 + z2)));
+                s2 = f_fma<CT>(x1, x1 + x2, f_fma<CT>(y1, y1 + y2, f_fma<CT>(z1, z1 + z2, s2)));
+                s2 = f_fma<CT>(x2, x2, f_fma<CT>(y2, y2, f_fma<CT>(z2, z2, s2)));
+                sm2 = f_fma<CT>(at, s2, sm2);
+                cur = nxt;
             }
-            acc += __popc(m);
+            const CT A_ = kA.value();
+            // distance from the site to the facet plane; tetrahedra (site, fan triangle) give
+            // V_f = dist A_f / 3, first moment dist * sum(at (v0+v1+v2)/3) / 4, second moment dist/30 * sum(at s2)
+            CT dist = pp.h * inrm;
+            kvol.add(dist * A_ * (CT)(1.0 / 3.0));
+            mzx += dist * csx * (CT)0.25;
+            mzy += dist * csy * (CT)0.25;
+            mzz += dist * csz * (CT)0.25;
+            m2 += dist * sm2 * (CT)(1.0 / 30.0);
+            if (fem) {
+                Face f;
+                f.dx = (float)pp.x; f.dy = (float)pp.y; f.dz = (float)pp.z;
+                f.area = (float)A_;
+                if (A_ != (CT)0) { f.cx = (float)(csx / A_); f.cy = (float)(csy / A_); f.cz = (float)(csz / A_); }
+                else { f.cx = f.cy = f.cz = 0.f; }
+                f.nbr = S.psrc[p];
+                A.faces[start + acc + __popc(fm & lanemask_lt())] = f;
+            }
         }
+        acc += __popc(fm);
+    }
+    kvol.warp_reduce();
+    CT vol = kvol.value();
+    m2 = warp_sum<CT>(m2);
+    mzx = warp_sum<CT>(mzx); mzy = warp_sum<CT>(mzy); mzz = warp_sum<CT>(mzz);
+    const CT sg = vol < 0 ? (CT)-1 : (CT)1;
+    vol *= sg; m2 *= sg;
+    if (sg < 0) {
+        // reversed orientation: the areas were written with the opposite sign
+        for (int k = (int)lane; k < nf_total; k += 32) A.faces[start + k].area = -A.faces[start + k].area;
     }
     if (lane == 0) {
         CellOut co;
