@@ -409,7 +409,8 @@ void vt_destroy(vt_handle h);
  * vt_release_memory -- handle workspaces come from a stream-ordered memory pool per device that the library
  * creates on first use (cudaMallocFromPoolAsync / cudaFreeAsync on the handle's stream), which keeps freed memory
  * for the next build instead of returning it to the device; this call synchronises the current device and gives
- * the pool's unused memory back.  Returns VT_OK or VT_ERR_CUDA.  (Not part of the paper's method.)
+ * the pool's unused memory back, and frees the pinned host blocks kept for the status reads of destroyed
+ * handles.  Returns VT_OK or VT_ERR_CUDA.  (Not part of the paper's method.)
  */
 int vt_release_memory(void);
 

@@ -128,6 +128,14 @@ void map_give(DevStatus* p) {
     g_map_free.push_back(p);
 }
 
+// give the kept blocks back to the system (those of live handles stay theirs)
+void map_release() {
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    for (DevStatus* p : g_map_free)
+        if (cudaFreeHost(p) != cudaSuccess) cudaGetLastError();
+    g_map_free.clear();
+}
+
 void free_handle(vt_handle h) {
     if (!h) return;
     for (int k = 0; k < 4; k++)
@@ -936,6 +944,7 @@ int vt_release_memory(void) {
         cudaGetLastError();
         return VT_ERR_CUDA;
     }
+    map_release();
     return cuda_rc(cudaMemPoolTrimTo(pool, 0));
 }
 
