@@ -1150,21 +1150,23 @@ __device__ __forceinline__ void test_slots(const WarpSmem<CT, TP>& S, unsigned* 
     for (int q = 0; q < TP; q++) masks[q] = 0u;
 }
 
-template <typename P, typename CT, bool EXACT, int TP>
+template <typename P, typename CT, bool EXACT, int TP, bool SETS>
 __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, double* xws,
                                     CellCounters& cc, bool small_box) {
     const P* spos = (const P*)A.spos;
     // geometry and sorted index range of the cell's point set
-    Geometry g = A.geo;
+    // a batch of sets: the cell's set; one set: the launch's box, read where it is used
+    Geometry gs;
     int64_t slo = 0, shi = A.N;
     int k_target = A.k_target;
-    if (A.sset) {
+    if (SETS) {
         const uint32_t s = A.sset[self];
-        g = A.sgeo[s];
+        gs = A.sgeo[s];
         slo = A.soff[s];
         shi = A.soff[s + 1];
         if (A.set_cfg) k_target = A.set_cfg[s] & 0xffff;
     }
+    const Geometry& g = SETS ? gs : A.geo;
     const unsigned lane = lane_id(), lt = lanemask_lt();
     const CT u = Prec<CT>::u();
     const P pi = spos[self];
@@ -1573,7 +1575,7 @@ __device__ int do_cell(WarpSmem<CT, TP>& S, const ClipArgs& A, uint32_t self, do
 // Fast kernels: Cap<4>, CLIP_WARPS warps per block, every cell; cells they cannot finish (an undecided FP64
 // test, an ill-conditioned vertex or a capacity overflow) are appended to the exact list.
 // Exact kernel: Cap<16>, one warp per block, the listed cells, exact predicates.
-template <typename P, typename CT, bool EXACT, int TP, int WPB>
+template <typename P, typename CT, bool EXACT, int TP, int WPB, bool SETS>
 __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
     extern __shared__ __align__(32) unsigned char smem_raw[];
     const int w = threadIdx.x >> 5;
@@ -1603,7 +1605,7 @@ __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
             int rc = 0;
 #pragma unroll 1
             for (int attempt = 0; attempt < 2; attempt++) {
-                rc = do_cell<P, CT, EXACT, TP>(S, A, self, xws, cc, !EXACT && attempt == 0);
+                rc = do_cell<P, CT, EXACT, TP, SETS>(S, A, self, xws, cc, !EXACT && attempt == 0);
                 if (rc != RC_RETRY_BOX) break;
             }
             VT_T1(cc, 5, tall);
@@ -1663,8 +1665,8 @@ __global__ void __launch_bounds__(WPB * 32) k_clip(ClipArgs A) {
 }  // namespace vt
 
 namespace vt {
-template <typename P, typename CT, bool EXACT>
-static void launch_one(const ClipArgs& a, int sm_count, cudaStream_t s) {
+template <typename P, typename CT, bool EXACT, bool SETS>
+static void launch_one_t(const ClipArgs& a, int sm_count, cudaStream_t s) {
     constexpr int TP = EXACT ? 16 : 4;
     constexpr int WPB = EXACT ? 1 : CLIP_WARPS;
     size_t smem = sizeof(WarpSmem<CT, TP>) * WPB;
@@ -1675,13 +1677,18 @@ static void launch_one(const ClipArgs& a, int sm_count, cudaStream_t s) {
     cudaGetDevice(&dev);
     int per_sm = (dev >= 0 && dev < 64) ? per_sm_dev[dev] : 0;
     if (per_sm == 0) {
-        cudaFuncSetAttribute(k_clip<P, CT, EXACT, TP, WPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip<P, CT, EXACT, TP, WPB>, WPB * 32, smem);
+        cudaFuncSetAttribute(k_clip<P, CT, EXACT, TP, WPB, SETS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_clip<P, CT, EXACT, TP, WPB, SETS>, WPB * 32, smem);
         if (per_sm < 1) per_sm = 1;
         if (dev >= 0 && dev < 64) per_sm_dev[dev] = per_sm;
     }
     int blocks = sm_count * per_sm;
     if (EXACT) blocks = a.xws_warps < blocks ? a.xws_warps : blocks;
-    k_clip<P, CT, EXACT, TP, WPB><<<blocks, WPB * 32, smem, s>>>(a);
+    k_clip<P, CT, EXACT, TP, WPB, SETS><<<blocks, WPB * 32, smem, s>>>(a);
+}
+template <typename P, typename CT, bool EXACT>
+static void launch_one(const ClipArgs& a, int sm_count, cudaStream_t s) {
+    if (a.sset) launch_one_t<P, CT, EXACT, true>(a, sm_count, s);
+    else launch_one_t<P, CT, EXACT, false>(a, sm_count, s);
 }
 }  // namespace vt
