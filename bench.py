@@ -52,9 +52,9 @@ WORK = {
     "halosets4096": {"n_cert": 147.19, "verts": 26.55, "faces": 15.27},
 }
 # DRAM bytes (read + write) of one launch of the clipping kernel: dram__bytes_read.sum + dram__bytes_write.sum of
-# one launch on the 2,097,152-point clustered set (582 B per cell, profiles/k_clip_clustered2M_dram.md) times the
+# one launch on the 2,097,152-point clustered set (543 B per cell, profiles/k_clip_clustered2M_dram.md) times the
 # cells of the launch (the facet records that dominate it grow with the cells)
-CLIP_TRAFFIC_PER_CELL = {"filter32": 581.7}
+CLIP_TRAFFIC_PER_CELL = {"filter32": 543.3}
 CLIP_TRAFFIC = {("clustered16M", "filter32"): CLIP_TRAFFIC_PER_CELL["filter32"] * 16777216,
                 ("clustered2M", "filter32"): CLIP_TRAFFIC_PER_CELL["filter32"] * 2097152}
 # FMA lanes per SM of the GB300 (sm_103): 128 FP32; the FP64 rate is 1/64 of it (2 FP64 FMA per clock per SM)
