@@ -1,4 +1,5 @@
-// vt_clip_thread.cu -- the bulk clipping kernel: one thread per cell, one warp per bucket of 32 cells.
+// vt_clip_thread.cu -- the bulk clipping kernels: one thread per cell (a warp per bucket of 32 cells), or 4 or 8
+// lanes per cell (further down); and the voxel-grid and weighted-moment kernels that rebuild cells from their facets.
 //
 // The warp kernel (vt_clip_impl.cuh) spends a whole warp on one cell, and most of its instructions on
 // cross-lane steps (candidate search, ballots, shuffles).  Here the 32 cells of a tree bucket (32 consecutive
